@@ -1,0 +1,455 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 near-field P2P operator: pair-interactions per second.
+
+Workload (default): the occupancy sweep on the unit sphere -- N = 2^20 points
+uniform on the sphere surface, leaf grids of 180^3 / 124^3 / 86^3 / 61^3 boxes
+(mean 8 / 16 / 32 / 64 points per non-empty box), leaf edge a quarter
+wavelength, Helmholtz kernel, complex64 strengths ~ N(0, 1), one right-hand
+side, FP32 arithmetic.  One step applies the operator once at each of the four
+occupancies (strength staging + pair kernel + scatter); the plans (binning,
+neighbour lists, packed layout) are built once per geometry before timing.
+
+value = pairs of the step / step time, pairs = ordered (target, source) pairs
+with r > 0 in every 27-box neighbourhood.  L2 is flushed (256 MiB write)
+between timed steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--layout auto|indexed|redundant]
+
+--impl reference times the FP64 CPU oracle, as it stands, on a bounded sample
+of targets of the same workload (no GPU use).  Under torchrun each rank runs
+an independent replica (the operator has no exchange step on one GPU per
+box set); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "P2P pair-interactions/s (G/s) + roofline fraction at stated L2 err vs FP64"
+UNIT = "Gpair/s"
+OCCUPANCIES = (8, 16, 32, 64)
+MUFU_PER_PAIR = {"helmholtz": 3, "laplace": 1}  # rsqrt, sin, cos per Helmholtz pair
+MUFU_LANES_PER_SM_CLK = 16
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+            "source": "fallback"}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# --------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id.lower() if bus_id else None
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        rows = self.rows
+        if self.bus_id:
+            mine = [r for r in rows if len(r) > 1 and self.bus_id.endswith(r[1].lower()[-12:])]
+            rows = mine or rows
+        sm = [float(r[2]) for r in rows if len(r) >= 10 and r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if len(r) >= 10 and r[3].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows if len(r) >= 10 for i in range(4) if r[6 + i] == "Active"})
+        power = [float(r[4]) for r in rows if len(r) >= 10 and r[4].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------- workload --
+
+def sweep_workloads():
+    from paper_2403_01596_gb300 import workloads as W
+    return [W.sphere_density(d) for d in OCCUPANCIES]
+
+
+def _sample_targets(n, count, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, size=min(count, n), replace=False))
+
+
+def _sample_pairs(struct_host, points, targets) -> int:
+    """Exact pair count of the sampled targets from the box structure (r > 0 pairs)."""
+    box_ptr, nbr_ptr, nbr_idx, point_box, perm = struct_host
+    sizes = np.diff(box_ptr)
+    total = 0
+    for i in targets:
+        b = point_box[i]
+        s = int(sizes[nbr_idx[nbr_ptr[b]:nbr_ptr[b + 1]]].sum())
+        own = perm[box_ptr[b]:box_ptr[b + 1]]
+        dup = int(np.all(points[own] == points[i], axis=1).sum())
+        total += s - dup
+    return total
+
+
+def cpu_oracle_sample(wls, structs, seconds_per_density: float, seed: int):
+    """Times the FP64 oracle (as it stands, single thread) on sampled targets."""
+    import oracle
+    from paper_2403_01596_gb300 import workloads as W
+    oracle.build()
+    res = []
+    for wl, st in zip(wls, structs):
+        lam = W.strengths(wl.n, 1, wl.seed)
+        # calibrate with a small call, then size the sample to the time budget
+        probe = _sample_targets(wl.n, 256, seed)
+        t = time.perf_counter()
+        oracle.p2p_targets(wl.points, lam, probe, wl.lo, wl.h, wl.ng, wl.k)
+        t_probe = time.perf_counter() - t
+        per_target = max(t_probe / len(probe), 1e-7)
+        m = int(min(wl.n, max(512, seconds_per_density / per_target)))
+        targets = _sample_targets(wl.n, m, seed + 1)
+        t = time.perf_counter()
+        ref = oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, wl.k)
+        dt = time.perf_counter() - t
+        pairs = _sample_pairs(st, wl.points, targets)
+        res.append({"occupancy": wl.meta["target_occupancy"], "targets": targets, "ref": ref, "seconds": dt,
+                    "pairs": pairs})
+    return res
+
+
+def host_structure(plan):
+    s = plan.structure
+    n = s.n
+    return (s.box_ptr.cpu().numpy(), s.nbr_ptr.cpu().numpy(), s.nbr_idx.cpu().numpy()[:s.nnz],
+            s.point_box.cpu().numpy()[:n], s.perm.cpu().numpy()[:n])
+
+
+def _oracle_structure(wl):
+    import oracle
+    b = oracle.bin_points(wl.points, wl.lo, wl.h, wl.ng)
+    nptr, nidx = oracle.neighbors(b["box_keys"], wl.ng)
+    return (b["box_ptr"], nptr, nidx, b["point_box"], b["perm"])
+
+
+# ------------------------------------------------------------ reference --
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from paper_2403_01596_gb300 import workloads as W
+    import oracle
+    oracle.build()
+    wls = sweep_workloads()
+    structs = [_oracle_structure(wl) for wl in wls]
+    lams = [W.strengths(wl.n, 1, wl.seed) for wl in wls]
+    per_density_s = 0.6
+    # size one step: ~per_density_s of oracle work per occupancy
+    samples = []
+    for i, wl in enumerate(wls):
+        probe = _sample_targets(wl.n, 256, 7)
+        t = time.perf_counter()
+        oracle.p2p_targets(wl.points, lams[i], probe, wl.lo, wl.h, wl.ng, wl.k)
+        per_target = max((time.perf_counter() - t) / len(probe), 1e-7)
+        samples.append(int(min(wl.n, max(256, per_density_s / per_target))))
+    times, pairs = [], []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        p = 0
+        for i, wl in enumerate(wls):
+            targets = _sample_targets(wl.n, samples[i], 1000 + step)
+            oracle.p2p_targets(wl.points, lams[i], targets, wl.lo, wl.h, wl.ng, wl.k)
+            p += _sample_pairs(structs[i], wl.points, targets) if step >= args.warmup else 0
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            pairs.append(p)
+    value = sum(pairs) / sum(times) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args, "oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step {samples} sampled targets (occupancy 8/16/32/64), FP64 single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _config(args, layout):
+    return {"workload": "sphere_occupancy_sweep", "n_points": 1 << 20, "occupancies": list(OCCUPANCIES),
+            "grids": [180, 124, 86, 61], "kernel": "helmholtz", "k": "2*pi/(4h)", "nrhs": 1, "layout": layout,
+            "l2": "flushed between timed steps (256 MiB write, outside the timed events)"}
+
+
+# ------------------------------------------------------------------- ours --
+
+def _traffic_for(kernel_src_hash: str, layout: str):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    e = d.get(layout)
+    if not e or e.get("source_sha256") != kernel_src_hash:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("p2p_apply.cu", "p2p_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2403_01596_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def run_ours(args):
+    import torch
+    from paper_2403_01596_gb300 import _capi as C
+    from paper_2403_01596_gb300 import api, workloads as W
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    wls = sweep_workloads()
+    pts = torch.from_numpy(wls[0].points).to(dev)
+    plans, lams, outs, pairs = [], [], [], []
+    layouts = []
+    t_plan = []
+    for wl in wls:
+        layout = args.layout
+        if layout == "auto":
+            from paper_2403_01596_gb300 import autotune
+            tune = autotune.best_config(wl, pts)
+            layout, tuning = tune["layout"], tune["tuning"]
+        else:
+            tuning = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k, layout=layout, tuning=tuning)
+        torch.cuda.synchronize()
+        t_plan.append(time.perf_counter() - t0)
+        plans.append(plan)
+        layouts.append(layout)
+        lam = torch.from_numpy(W.strengths(wl.n, 1, wl.seed)).to(dev)
+        lams.append(lam)
+        outs.append(torch.empty_like(lam))
+        pairs.append(plan.pair_count())
+    step_pairs = sum(pairs)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    path = C.P2P_PATH_FP32_SHARED
+
+    def one_apply(i, evs=None):
+        p = plans[i]
+        if evs:
+            evs[0].record(stream)
+        C.p2p_apply_stage(p._plan, lams[i], 1, 1, path, stream)
+        if evs:
+            evs[1].record(stream)
+        C.p2p_apply_staged(p._plan, outs[i], 1, 1, 0, path, stream)
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        for i in range(len(plans)):
+            one_apply(i)
+    torch.cuda.synchronize()
+    nd = len(plans)
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nd)] for _ in range(args.steps)]
+    bus = None
+    try:
+        bus = "%04x:%02x:%02x" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except AttributeError:
+        bus = None
+    clocks = ClockSampler(bus)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        for i in range(nd):
+            one_apply(i, evs[s][i])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [evs[s][0][0].elapsed_time(evs[s][nd - 1][2]) for s in range(args.steps)]
+    pair_ms = [[evs[s][i][1].elapsed_time(evs[s][i][2]) for s in range(args.steps)] for i in range(nd)]
+    stage_ms = [[evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps)] for i in range(nd)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * step_pairs / (ms_per_step * 1e-3) / 1e9
+
+    # ---------------- end to end through the public API with host buffers
+    host_lam = [lam.cpu().pin_memory() for lam in lams]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_lam]
+    dev_lam = [torch.empty_like(lam) for lam in lams]
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(nd):
+            dev_lam[i].copy_(host_lam[i], non_blocking=True)
+            plans[i].apply(dev_lam[i], out=outs[i].view(-1, 1))
+            host_out[i].copy_(outs[i], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_bytes = sum(h.numel() * 8 for h in host_lam)
+    e2e_value = world * step_pairs / (statistics.mean(e2e_ms) * 1e-3) / 1e9
+
+    # ---------------- roofline of the dominant kernel (the pair kernel)
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_pairs = sms * MUFU_LANES_PER_SM_CLK * f_max / MUFU_PER_PAIR["helmholtz"] / 1e9
+    pair_total_ms = sum(statistics.mean(pm) for pm in pair_ms)
+    achieved = step_pairs / (pair_total_ms * 1e-3) / 1e9
+    detail = []
+    for i, wl in enumerate(wls):
+        pm, sm = statistics.mean(pair_ms[i]), statistics.mean(stage_ms[i])
+        detail.append({"occupancy": wl.meta["target_occupancy"], "layout": layouts[i], "boxes": plans[i].num_boxes,
+                       "pairs": pairs[i], "pair_kernel_ms": pm, "stage_ms": sm,
+                       "gpair_s": pairs[i] / (pm + sm) / 1e6, "pair_kernel_frac_of_mufu": pairs[i] / pm / 1e6 / peak_pairs,
+                       "plan_s": t_plan[i], "work_items": plans[i].info["work_items"]})
+    khash = _kernel_hash()
+    traffic = _traffic_for(khash, layouts[0]) if len(set(layouts)) == 1 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_pairs, "unit": "Gpair/s",
+                "frac": achieved / peak_pairs, "traffic": traffic,
+                "kernel": "k_pair (FP32 box-per-warp P2P)",
+                "peak_basis": f"MUFU: {sms} SMs x 16 lanes/clk x {f_max / 1e6:.0f} MHz / 3 MUFU per Helmholtz pair "
+                              f"(sm_max_mhz {peaks['source']})",
+                "peak_at_measured_clock": (sms * 16 * clk["sm_mhz"] * 1e6 / 3 / 1e9) if clk.get("sm_mhz") else None,
+                "per_occupancy": detail}
+
+    # ---------------- CPU oracle baseline and sampled accuracy (rank 0, N = 1)
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        structs = [host_structure(p) for p in plans]
+        res = cpu_oracle_sample(wls, structs, args.cpu_seconds / len(wls), 17)
+        cpu_pairs = sum(r["pairs"] for r in res)
+        cpu_s = sum(r["seconds"] for r in res)
+        cpu = {"value": cpu_pairs / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle on " + ", ".join(f"{len(r['targets'])} targets at occupancy {r['occupancy']}"
+                                                       for r in res) + f" ({cpu_pairs} pairs, {cpu_s:.1f} s)"}
+        errs = []
+        for r, out in zip(res, outs):
+            got = out.cpu().numpy()[r["targets"]]
+            errs.append(float(np.linalg.norm(got - r["ref"]) / np.linalg.norm(r["ref"])))
+        err = {"rel_l2_max": max(errs), "per_occupancy": errs, "sample": "targets of the cpu_baseline sample",
+               "tolerance": 1e-5}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(args, layouts[0] if len(set(layouts)) == 1 else "per-occupancy:" + ",".join(layouts)),
+            "pairs_per_step": step_pairs * world, "rel_l2_vs_fp64": err,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
+            "gpu_launches": 2 * nd * args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "wall_s_timed_region": wall, "device": props.name, "sms": sms,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--layout", choices=("auto", "indexed", "redundant"), default="indexed")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: warmup raised to 3 (timing rule)", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,266 @@
+/*
+ * p2p.h -- C ABI of the GB300 near-field P2P library (libp2p.so).
+ *
+ * The near-field (P2P) operator of MLFMA (Sec. 1: A = A_near + A_far; the
+ * near part is evaluated directly): for every target point x_i,
+ *
+ *     out_i = sum over sources y_j in the leaf box of x_i and in the (up to 26)
+ *             leaf boxes adjacent to it, r_ij = |x_i - y_j| > 0, of G(r_ij) lambda_j
+ *
+ * with G(r) = exp(i k r) / (4 pi r) (Helmholtz) or 1 / (4 pi r) (Laplace).
+ * Sources and targets are one point set, as in the paper's symmetric setup
+ * (Sec. 3.1).  Leaf boxes form a uniform grid of ng^3 cubes of edge h starting
+ * at lo; boxes are numbered in Morton order over the non-empty boxes only
+ * (Sec. 3.2 stores box data "in the order of the box's Morton index").
+ *
+ * Two source layouts are offered (Sec. 3.2 "indexing", Sec. 3.3 "repetition"):
+ *   P2P_LAYOUT_INDEXED    every box reads its neighbours' sources through the
+ *                         neighbour lists from one box-sorted point array;
+ *   P2P_LAYOUT_REDUNDANT  every box owns a contiguous copy of all sources of its
+ *                         neighbourhood (the redundancy of Sec. 3.3, kept per box
+ *                         rather than per target), so each thread block reads one
+ *                         contiguous tile independent of all others.
+ *
+ * Conventions shared by every entry point
+ *   - Memory.  Pointers marked [dev] are CUDA device pointers, [host] are host
+ *     pointers.  The caller allocates and owns every buffer, including the
+ *     workspaces whose sizes the *_workspace_size queries return.  The library
+ *     never frees caller memory.  A plan stores pointers to the arrays it was
+ *     created from; they must stay valid and unchanged for the plan's lifetime.
+ *   - Streams.  Every call enqueues its work on `stream` (a cudaStream_t; NULL
+ *     is the legacy default stream) and returns without waiting, except where a
+ *     call says it synchronises (it then waits for `stream` only).
+ *   - Point order.  Coordinates, strengths, results and gradients are in the
+ *     caller's original point order.  perm maps sorted position -> original index.
+ *   - Complex numbers are two consecutive floats (re, im) (C99 float complex,
+ *     CUDA float2); a complex array of n rows and nrhs columns with leading
+ *     dimension ld stores element (i, q) at index i*ld + q, ld >= nrhs.
+ *   - Errors.  Every call returns a p2p_status and never throws or aborts.
+ *     Invalid arguments return P2P_ERR_INVALID before any work is enqueued.  A
+ *     CUDA launch or runtime failure returns P2P_ERR_CUDA; p2p_last_error_string
+ *     gives the CUDA message.  Anomalies detected inside kernels (a bounded wait
+ *     that ran out, an out-of-range index in the input structure) set a device
+ *     status word that p2p_last_async_status reads.
+ */
+#ifndef P2P_H
+#define P2P_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define P2P_API __attribute__((visibility("default")))
+#else
+#define P2P_API
+#endif
+
+typedef struct CUstream_st* p2p_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    P2P_OK = 0,
+    P2P_ERR_INVALID = 1,     /* bad argument, size, pointer alignment or input value */
+    P2P_ERR_WORKSPACE = 2,   /* workspace smaller than the size query returned */
+    P2P_ERR_CUDA = 3,        /* a CUDA call failed; see p2p_last_error_string */
+    P2P_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+    P2P_ERR_UNSUPPORTED = 5, /* valid request that this build/device does not support */
+    P2P_ERR_ALLOC = 6        /* host memory for the plan object could not be allocated */
+} p2p_status;
+
+typedef enum { P2P_HELMHOLTZ = 0, P2P_LAPLACE = 1 } p2p_kernel;
+
+typedef enum { P2P_LAYOUT_INDEXED = 0, P2P_LAYOUT_REDUNDANT = 1 } p2p_layout;
+
+/* Evaluation path of p2p_apply_path (the plain p2p_apply picks P2P_PATH_AUTO). */
+typedef enum {
+    P2P_PATH_AUTO = 0,        /* FP32 shared-G for nrhs < 16, tensor-core path otherwise */
+    P2P_PATH_FP32_PER_RHS = 1,/* FP32; G re-evaluated for every right-hand side */
+    P2P_PATH_FP32_SHARED = 2, /* FP32; each G evaluated once and applied to up to 8 RHS */
+    P2P_PATH_TC_BF16X3 = 3    /* G tile split into BF16 hi + lo, 3 tcgen05 MMAs, FP32 accumulate */
+} p2p_path;
+
+/* Launch tuning of a plan (the autotuner's knobs).  Zero fields take defaults. */
+typedef struct {
+    int32_t chunk;         /* sources staged per work item, multiple of 32, 32..1024 (default 128) */
+    int32_t warps_per_cta; /* warps per thread block of the pair kernel, 1..16 (default 8) */
+    int32_t target_group;  /* targets per work item, multiple of 32, 32..128 (default 128) */
+    int32_t reserved;
+} p2p_tuning;
+
+typedef struct p2p_plan p2p_plan;
+
+/* ------------------------------------------------------------ messages --- */
+
+/* Static description of a status code. */
+P2P_API const char* p2p_status_string(p2p_status status);
+
+/* Message of the last CUDA failure seen by this thread ("" if none). */
+P2P_API const char* p2p_last_error_string(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+P2P_API int32_t p2p_version(void);
+
+/* ------------------------------------------------------- leaf binning --- */
+/*
+ * Sec. 3.1 (points assigned to the boxes of the last tree level) and Sec. 3.2
+ * (box data in Morton order).  For every point, per axis
+ *     cell = clamp(floor((double(x) - lo) / h), 0, ng - 1)
+ * computed as one IEEE double subtraction and one double division (so the
+ * result equals a host computation bit for bit); the Morton key interleaves
+ * the cell bits with x at bit 0, y at bit 1, z at bit 2 of every triple.  A
+ * point on a face between cells belongs to the upper cell; points outside the
+ * grid are clamped into the boundary boxes.  Points are stably sorted by key
+ * (ties keep the original order) and run-length encoded into boxes.
+ *
+ *   pts        [dev]  n x 3 float, xyz of each point (row-major, 4-byte aligned)
+ *   n                 number of points, 0 <= n < 2^31 - 1
+ *   lo         [host] 3 doubles, grid origin
+ *   h                 leaf box edge, > 0 and finite
+ *   ng                boxes per axis, 1 <= ng <= 2^21
+ *   perm       [dev]  out, n int32: perm[s] = original index of the s-th sorted point
+ *   point_box  [dev]  out, n int32: box id of each original point
+ *   box_keys   [dev]  out, capacity n int64: Morton key of each box (ascending)
+ *   box_ptr    [dev]  out, capacity n + 1 int32: box b holds sorted points box_ptr[b] .. box_ptr[b+1]-1
+ *   num_boxes  [host] out, number of non-empty boxes
+ *   work       [dev]  scratch of at least p2p_bin_workspace_size(n) bytes, 256-byte aligned
+ *
+ * Synchronises: waits for `stream` to read back num_boxes and the input check.
+ * Returns P2P_ERR_INVALID if a coordinate is NaN or infinite (outputs are then
+ * undefined).
+ */
+P2P_API p2p_status p2p_bin_workspace_size(int64_t n, size_t* bytes);
+P2P_API p2p_status p2p_bin_points(const float* pts, int64_t n, const double lo[3], double h, int32_t ng,
+                                  int32_t* perm, int32_t* point_box, int64_t* box_keys, int32_t* box_ptr,
+                                  int32_t* num_boxes, void* work, size_t work_bytes, p2p_stream_t stream);
+
+/* ---------------------------------------------------- neighbour lists --- */
+/*
+ * Sec. 3.2 (the per-box list of neighbouring sources and its "second order
+ * index") with the 9 adjacent boxes of the paper's 2D quadtree replaced by
+ * the 27 boxes of a 3D grid: the neighbours of box b are the non-empty boxes
+ * whose cells lie within Chebyshev distance 1 of b's cell, b itself included,
+ * with no periodic wrap, listed in ascending box id.
+ *
+ *   box_keys   [dev]  num_boxes int64 from p2p_bin_points (strictly ascending)
+ *   box_ptr    [dev]  num_boxes + 1 int32 from p2p_bin_points
+ *   num_boxes, ng     as returned / passed to p2p_bin_points
+ *   nbr_ptr    [dev]  out, num_boxes + 1 int32 (CSR row pointer)
+ *   nbr_idx    [dev]  out, capacity 27 * num_boxes int32 (CSR column indices)
+ *   nnz        [host] out, number of (box, neighbour) entries = nbr_ptr[num_boxes]
+ *   sources    [host] out, sum over boxes of the number of sources in the
+ *                     box's neighbourhood (the size of the redundant layout)
+ *   work       [dev]  scratch of at least p2p_neighbors_workspace_size bytes
+ *
+ * Synchronises to read back nnz and sources.
+ */
+P2P_API p2p_status p2p_neighbors_workspace_size(int32_t num_boxes, size_t* bytes);
+P2P_API p2p_status p2p_build_neighbors(const int64_t* box_keys, const int32_t* box_ptr, int32_t num_boxes,
+                                       int32_t ng, int32_t* nbr_ptr, int32_t* nbr_idx, int64_t* nnz,
+                                       int64_t* sources, void* work, size_t work_bytes, p2p_stream_t stream);
+
+/* ------------------------------------------------------------- plans --- */
+/*
+ * A plan binds one point set and its box structure to a kernel, a wavenumber,
+ * a source layout and launch tuning, and lays the device data out for the
+ * apply calls: box-sorted coordinates, the work-item list (target group x
+ * source chunk of one box), and for P2P_LAYOUT_REDUNDANT the per-box packed
+ * copy of the neighbourhood's source coordinates (the data collection of Sec.
+ * 3.3, eq. 6 - 8, done on the device).
+ *
+ *   pts                    [dev] n x 3 float (the array given to p2p_bin_points)
+ *   perm, box_ptr          [dev] from p2p_bin_points
+ *   nbr_ptr, nbr_idx       [dev] from p2p_build_neighbors
+ *   nnz, sources                 from p2p_build_neighbors
+ *   kernel, k                    Green's function and wavenumber (k finite; ignored for Laplace)
+ *   layout                       source layout
+ *   max_nrhs                     largest nrhs any apply on this plan will use, 1..256
+ *   tuning                 [host] NULL for defaults
+ *   workspace              [dev] at least p2p_plan_workspace_size bytes, 256-byte aligned;
+ *                                owned by the caller, must outlive the plan
+ *
+ * Synchronises to read back the number of work items.  The plan object
+ * itself is host memory released by p2p_plan_destroy.
+ */
+P2P_API p2p_status p2p_plan_workspace_size(int64_t n, int32_t num_boxes, int64_t nnz, int64_t sources,
+                                           p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
+                                           size_t* bytes);
+P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n, const int32_t* perm,
+                                   const int32_t* box_ptr, int32_t num_boxes, const int32_t* nbr_ptr,
+                                   const int32_t* nbr_idx, int64_t nnz, int64_t sources, p2p_kernel kernel,
+                                   float k, p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
+                                   void* workspace, size_t workspace_bytes, p2p_stream_t stream);
+P2P_API p2p_status p2p_plan_destroy(p2p_plan* plan);
+
+/* Number of work items, ordered (target, source) pairs with r > 0 are not
+ * counted here; see p2p_plan_pair_count. */
+P2P_API p2p_status p2p_plan_info(const p2p_plan* plan, int64_t* n, int32_t* num_boxes, int64_t* sources,
+                                 int64_t* work_items, p2p_layout* layout, p2p_tuning* tuning);
+
+/* Number of ordered (target, source) pairs in the neighbourhoods with r > 0
+ * (the work of one apply per right-hand side).  Synchronises. */
+P2P_API p2p_status p2p_plan_pair_count(const p2p_plan* plan, int64_t* pairs, p2p_stream_t stream);
+
+/* ------------------------------------------------------------- apply --- */
+/*
+ * out = A lambda (p2p_apply), out = A^H g (p2p_apply_adjoint).  A is complex
+ * symmetric (G(x, y) = G(y, x) and the neighbour relation is symmetric), so
+ * A^H = conj(A): the adjoint uses exp(-i k r) / (4 pi r).  This is the
+ * gradient dL/dlambda of a real loss whose gradient with respect to out is g
+ * (convention dL/dRe + i dL/dIm).
+ *
+ *   lambda, g  [dev] n x nrhs complex64, leading dimension ld, 8-byte aligned
+ *   out        [dev] n x nrhs complex64, leading dimension ld; fully overwritten
+ *                    in its first nrhs columns, other columns untouched
+ *   nrhs             1 .. the plan's max_nrhs
+ *
+ * lambda and out must not overlap.  Calls on one plan must not overlap in
+ * time (they share the plan's staging buffers): issue them on one stream.
+ */
+P2P_API p2p_status p2p_apply(const p2p_plan* plan, const void* lambda, void* out, int32_t nrhs, int64_t ld,
+                             p2p_stream_t stream);
+P2P_API p2p_status p2p_apply_adjoint(const p2p_plan* plan, const void* g, void* out, int32_t nrhs, int64_t ld,
+                                     p2p_stream_t stream);
+
+/* p2p_apply / p2p_apply_adjoint with an explicit evaluation path. */
+P2P_API p2p_status p2p_apply_path(const p2p_plan* plan, const void* lambda, void* out, int32_t nrhs, int64_t ld,
+                                  int32_t adjoint, p2p_path path, p2p_stream_t stream);
+
+/*
+ * The two phases of p2p_apply_path, for callers that overlap or time them
+ * separately.  p2p_apply_stage gathers lambda into the plan's staging buffer
+ * in the order the chosen path reads it (box-sorted rows, or the per-box
+ * packed rows of the redundant layout, Sec. 3.3); p2p_apply_staged then runs
+ * the pair kernel on the staged strengths and writes out.  Both must be given
+ * the same nrhs and path; no other call on the plan may come between them.
+ * The arguments mean what they mean for p2p_apply_path.
+ */
+P2P_API p2p_status p2p_apply_stage(const p2p_plan* plan, const void* lambda, int32_t nrhs, int64_t ld, p2p_path path,
+                                   p2p_stream_t stream);
+P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrhs, int64_t ld, int32_t adjoint,
+                                    p2p_path path, p2p_stream_t stream);
+
+/*
+ * Gradient with respect to the point coordinates of a real loss L whose
+ * gradient with respect to out = A lambda is g, box membership held fixed:
+ *
+ *   dL/dx_m = sum_{j in nbr(m), r > 0} sum_q Re[G'(r) (conj(g_mq) lambda_jq + conj(g_jq) lambda_mq)] (x_m - x_j) / r
+ *
+ * with G'(r) = exp(ikr)(ikr - 1)/(4 pi r^2) (Helmholtz) or -1/(4 pi r^2) (Laplace).
+ *
+ *   lambda, g  [dev] n x nrhs complex64, leading dimension ld
+ *   grad       [dev] out, n x 3 float, overwritten
+ */
+P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, const void* g, float* grad,
+                                   int32_t nrhs, int64_t ld, p2p_stream_t stream);
+
+/* Reads and clears the plan's device status word.  Synchronises. */
+P2P_API p2p_status p2p_last_async_status(const p2p_plan* plan, p2p_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P2P_H */

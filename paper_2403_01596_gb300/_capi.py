@@ -1,0 +1,226 @@
+"""ctypes binding of libp2p.so: the C ABI of include/p2p.h with the same names.
+
+Argument marshalling only: every step of the operator runs in the library's
+CUDA kernels.  Tensors are passed as raw device pointers, streams as the
+cudaStream_t handle of a torch.cuda.Stream.  A missing library raises at first
+use; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+P2P_OK = 0
+P2P_ERR_INVALID = 1
+P2P_ERR_WORKSPACE = 2
+P2P_ERR_CUDA = 3
+P2P_ERR_TIMEOUT = 4
+P2P_ERR_UNSUPPORTED = 5
+P2P_ERR_ALLOC = 6
+
+P2P_HELMHOLTZ = 0
+P2P_LAPLACE = 1
+P2P_LAYOUT_INDEXED = 0
+P2P_LAYOUT_REDUNDANT = 1
+P2P_PATH_AUTO = 0
+P2P_PATH_FP32_PER_RHS = 1
+P2P_PATH_FP32_SHARED = 2
+P2P_PATH_TC_BF16X3 = 3
+
+_lock = threading.Lock()
+_lib = None
+
+
+class P2PError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        lib = _lib
+        msg = lib.p2p_status_string(status).decode() if lib else str(status)
+        detail = lib.p2p_last_error_string().decode() if (lib and status == P2P_ERR_CUDA) else ""
+        super().__init__(f"{where}: {msg}" + (f" ({detail})" if detail else ""))
+
+
+class p2p_tuning(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("target_group", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libp2p.so (building it in-tree first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libp2p.so not found at {path}")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P, i32, i64, sz, dbl, flt = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t,
+                                      ctypes.c_double, ctypes.c_float)
+        PI64, PI32, PSZ = ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(sz)
+        sigs = {
+            "p2p_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "p2p_last_error_string": ([], ctypes.c_char_p),
+            "p2p_version": ([], i32),
+            "p2p_bin_workspace_size": ([i64, PSZ], ctypes.c_int),
+            "p2p_bin_points": ([P, i64, P, dbl, i32, P, P, P, P, PI32, P, sz, P], ctypes.c_int),
+            "p2p_neighbors_workspace_size": ([i32, PSZ], ctypes.c_int),
+            "p2p_build_neighbors": ([P, P, i32, i32, P, P, PI64, PI64, P, sz, P], ctypes.c_int),
+            "p2p_plan_workspace_size": ([i64, i32, i64, i64, ctypes.c_int, i32, P, PSZ], ctypes.c_int),
+            "p2p_plan_create": ([ctypes.POINTER(P), P, i64, P, P, i32, P, P, i64, i64, ctypes.c_int, flt,
+                                 ctypes.c_int, i32, P, P, sz, P], ctypes.c_int),
+            "p2p_plan_destroy": ([P], ctypes.c_int),
+            "p2p_plan_info": ([P, PI64, PI32, PI64, PI64, ctypes.POINTER(ctypes.c_int), P], ctypes.c_int),
+            "p2p_plan_pair_count": ([P, PI64, P], ctypes.c_int),
+            "p2p_apply": ([P, P, P, i32, i64, P], ctypes.c_int),
+            "p2p_apply_adjoint": ([P, P, P, i32, i64, P], ctypes.c_int),
+            "p2p_apply_path": ([P, P, P, i32, i64, i32, ctypes.c_int, P], ctypes.c_int),
+            "p2p_apply_stage": ([P, P, i32, i64, ctypes.c_int, P], ctypes.c_int),
+            "p2p_apply_staged": ([P, P, i32, i64, i32, ctypes.c_int, P], ctypes.c_int),
+            "p2p_grad_points": ([P, P, P, P, i32, i64, P], ctypes.c_int),
+            "p2p_last_async_status": ([P, P], ctypes.c_int),
+        }
+        for name, (args, res) in sigs.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def check(status: int, where: str):
+    if status != P2P_OK:
+        raise P2PError(status, where)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if stream is None else int(stream.cuda_stream))
+
+
+def _lo(lo):
+    return (ctypes.c_double * 3)(*[float(v) for v in lo])
+
+
+# --------------------------------------------------------------- C ABI calls --
+
+def p2p_bin_workspace_size(n: int) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().p2p_bin_workspace_size(n, ctypes.byref(out)), "p2p_bin_workspace_size")
+    return out.value
+
+
+def p2p_bin_points(pts, lo, h, ng, perm, point_box, box_keys, box_ptr, work, stream=None) -> int:
+    nb = ctypes.c_int32(0)
+    st = load().p2p_bin_points(_ptr(pts), pts.shape[0], _lo(lo), float(h), int(ng), _ptr(perm), _ptr(point_box),
+                               _ptr(box_keys), _ptr(box_ptr), ctypes.byref(nb), _ptr(work), work.numel(),
+                               _stream(stream))
+    check(st, "p2p_bin_points")
+    return nb.value
+
+
+def p2p_neighbors_workspace_size(num_boxes: int) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().p2p_neighbors_workspace_size(num_boxes, ctypes.byref(out)), "p2p_neighbors_workspace_size")
+    return out.value
+
+
+def p2p_build_neighbors(box_keys, box_ptr, num_boxes, ng, nbr_ptr, nbr_idx, work, stream=None):
+    nnz, src = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = load().p2p_build_neighbors(_ptr(box_keys), _ptr(box_ptr), int(num_boxes), int(ng), _ptr(nbr_ptr),
+                                    _ptr(nbr_idx), ctypes.byref(nnz), ctypes.byref(src), _ptr(work), work.numel(),
+                                    _stream(stream))
+    check(st, "p2p_build_neighbors")
+    return nnz.value, src.value
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    return ctypes.byref(p2p_tuning(int(t.get("chunk", 0)), int(t.get("warps_per_cta", 0)),
+                                   int(t.get("target_group", 0)), 0))
+
+
+def p2p_plan_workspace_size(n, num_boxes, nnz, sources, layout, max_nrhs, tuning=None) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().p2p_plan_workspace_size(n, num_boxes, nnz, sources, layout, max_nrhs, _tuning(tuning),
+                                         ctypes.byref(out)), "p2p_plan_workspace_size")
+    return out.value
+
+
+def p2p_plan_create(pts, perm, box_ptr, num_boxes, nbr_ptr, nbr_idx, nnz, sources, kernel, k, layout, max_nrhs,
+                    tuning, workspace, stream=None) -> ctypes.c_void_p:
+    plan = ctypes.c_void_p(0)
+    st = load().p2p_plan_create(ctypes.byref(plan), _ptr(pts), pts.shape[0], _ptr(perm), _ptr(box_ptr),
+                                int(num_boxes), _ptr(nbr_ptr), _ptr(nbr_idx), int(nnz), int(sources), int(kernel),
+                                float(k), int(layout), int(max_nrhs), _tuning(tuning), _ptr(workspace),
+                                workspace.numel(), _stream(stream))
+    check(st, "p2p_plan_create")
+    return plan
+
+
+def p2p_plan_destroy(plan):
+    if plan:
+        load().p2p_plan_destroy(plan)
+
+
+def p2p_plan_info(plan) -> dict:
+    n, nb, src, items = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    layout = ctypes.c_int(0)
+    t = p2p_tuning()
+    check(load().p2p_plan_info(plan, ctypes.byref(n), ctypes.byref(nb), ctypes.byref(src), ctypes.byref(items),
+                               ctypes.byref(layout), ctypes.byref(t)), "p2p_plan_info")
+    return {"n": n.value, "num_boxes": nb.value, "sources": src.value, "work_items": items.value,
+            "layout": layout.value, "tuning": {"chunk": t.chunk, "warps_per_cta": t.warps_per_cta,
+                                               "target_group": t.target_group}}
+
+
+def p2p_plan_pair_count(plan, stream=None) -> int:
+    out = ctypes.c_int64(0)
+    check(load().p2p_plan_pair_count(plan, ctypes.byref(out), _stream(stream)), "p2p_plan_pair_count")
+    return out.value
+
+
+def p2p_apply(plan, lam, out, nrhs, ld, stream=None):
+    check(load().p2p_apply(plan, _ptr(lam), _ptr(out), int(nrhs), int(ld), _stream(stream)), "p2p_apply")
+
+
+def p2p_apply_adjoint(plan, g, out, nrhs, ld, stream=None):
+    check(load().p2p_apply_adjoint(plan, _ptr(g), _ptr(out), int(nrhs), int(ld), _stream(stream)),
+          "p2p_apply_adjoint")
+
+
+def p2p_apply_path(plan, lam, out, nrhs, ld, adjoint, path, stream=None):
+    check(load().p2p_apply_path(plan, _ptr(lam), _ptr(out), int(nrhs), int(ld), int(adjoint), int(path),
+                                _stream(stream)), "p2p_apply_path")
+
+
+def p2p_apply_stage(plan, lam, nrhs, ld, path, stream=None):
+    check(load().p2p_apply_stage(plan, _ptr(lam), int(nrhs), int(ld), int(path), _stream(stream)),
+          "p2p_apply_stage")
+
+
+def p2p_apply_staged(plan, out, nrhs, ld, adjoint, path, stream=None):
+    check(load().p2p_apply_staged(plan, _ptr(out), int(nrhs), int(ld), int(adjoint), int(path), _stream(stream)),
+          "p2p_apply_staged")
+
+
+def p2p_grad_points(plan, lam, g, grad, nrhs, ld, stream=None):
+    check(load().p2p_grad_points(plan, _ptr(lam), _ptr(g), _ptr(grad), int(nrhs), int(ld), _stream(stream)),
+          "p2p_grad_points")
+
+
+def p2p_last_async_status(plan, stream=None) -> int:
+    return load().p2p_last_async_status(plan, _stream(stream))

@@ -1,0 +1,179 @@
+"""Python API of the GB300 P2P library on top of the C ABI.
+
+    plan = Plan(points, lo, h, ng, k, kernel="helmholtz", layout="indexed")
+    out = plan.apply(lam)                 # out = A lam   (complex64, original point order)
+    gl = plan.apply(g, adjoint=True)      # A^H g
+    gx = plan.grad_points(lam, g)         # dL/dx for dL/dout = g
+    out = p2p(lam, points, plan)          # autograd-aware: d/dlam and d/dpoints
+
+All device memory is owned by the Plan as torch tensors; the library only
+receives raw pointers.  Everything runs on the current CUDA stream.  There is
+no CPU fallback: points must be a CUDA tensor and libp2p.so must be loadable.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import _capi as C
+
+KERNELS = {"helmholtz": C.P2P_HELMHOLTZ, "laplace": C.P2P_LAPLACE}
+LAYOUTS = {"indexed": C.P2P_LAYOUT_INDEXED, "redundant": C.P2P_LAYOUT_REDUNDANT}
+PATHS = {"auto": C.P2P_PATH_AUTO, "fp32_per_rhs": C.P2P_PATH_FP32_PER_RHS, "fp32_shared": C.P2P_PATH_FP32_SHARED,
+         "tc_bf16x3": C.P2P_PATH_TC_BF16X3}
+
+
+def _stream():
+    return torch.cuda.current_stream()
+
+
+def _bytes(n: int, device) -> torch.Tensor:
+    # torch's caching allocator returns blocks aligned to at least 512 bytes
+    return torch.empty(max(int(n), 1), dtype=torch.uint8, device=device)
+
+
+class BoxStructure:
+    """Leaf binning + neighbour lists of one point set (device tensors)."""
+
+    def __init__(self, points: torch.Tensor, lo, h: float, ng: int):
+        if not points.is_cuda:
+            raise RuntimeError("P2P requires CUDA tensors (no CPU path)")
+        if points.dtype != torch.float32 or points.dim() != 2 or points.shape[1] != 3:
+            raise ValueError("points must be a float32 tensor of shape (n, 3)")
+        self.points = points.contiguous()
+        self.lo, self.h, self.ng = tuple(float(v) for v in lo), float(h), int(ng)
+        n = self.points.shape[0]
+        dev = self.points.device
+        s = _stream()
+        self.perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        self.point_box = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        keys = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+        ptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        work = _bytes(C.p2p_bin_workspace_size(n), dev)
+        self.num_boxes = C.p2p_bin_points(self.points, self.lo, self.h, self.ng, self.perm, self.point_box, keys, ptr,
+                                          work, s)
+        del work
+        B = self.num_boxes
+        self.box_keys = keys[:B].clone() if B else keys[:0]
+        self.box_ptr = ptr[:B + 1].clone()
+        self.nbr_ptr = torch.empty(B + 1, dtype=torch.int32, device=dev)
+        self.nbr_idx = torch.empty(max(27 * B, 1), dtype=torch.int32, device=dev)
+        work = _bytes(C.p2p_neighbors_workspace_size(B), dev)
+        self.nnz, self.sources = C.p2p_build_neighbors(self.box_keys, self.box_ptr, B, self.ng, self.nbr_ptr,
+                                                       self.nbr_idx, work, s)
+        del work
+        self.n = n
+
+
+class Plan:
+    """A P2P operator bound to a point set, kernel, wavenumber and source layout."""
+
+    def __init__(self, points: torch.Tensor, lo, h: float, ng: int, k: float = 0.0, kernel: str = "helmholtz",
+                 layout: str = "indexed", max_nrhs: int = 1, tuning: dict | None = None,
+                 structure: BoxStructure | None = None):
+        self.structure = structure if structure is not None else BoxStructure(points, lo, h, ng)
+        st = self.structure
+        self.kernel, self.layout, self.k = kernel, layout, float(k)
+        self.max_nrhs = int(max_nrhs)
+        self.tuning = tuning
+        dev = st.points.device
+        ws = C.p2p_plan_workspace_size(st.n, st.num_boxes, st.nnz, st.sources, LAYOUTS[layout], self.max_nrhs,
+                                       tuning)
+        self.workspace = _bytes(ws, dev)
+        self._plan = C.p2p_plan_create(st.points, st.perm, st.box_ptr, st.num_boxes, st.nbr_ptr, st.nbr_idx, st.nnz,
+                                       st.sources, KERNELS[kernel], self.k, LAYOUTS[layout], self.max_nrhs, tuning,
+                                       self.workspace, _stream())
+        self.info = C.p2p_plan_info(self._plan)
+        self._pairs = None
+
+    # ----------------------------------------------------------------- info --
+    @property
+    def n(self) -> int:
+        return self.structure.n
+
+    @property
+    def num_boxes(self) -> int:
+        return self.structure.num_boxes
+
+    def pair_count(self) -> int:
+        if self._pairs is None:
+            self._pairs = C.p2p_plan_pair_count(self._plan, _stream())
+        return self._pairs
+
+    def async_status(self) -> int:
+        return C.p2p_last_async_status(self._plan, _stream())
+
+    # ---------------------------------------------------------------- apply --
+    def _check_lam(self, lam: torch.Tensor):
+        if not lam.is_cuda or lam.dtype != torch.complex64:
+            raise ValueError("strengths must be a complex64 CUDA tensor")
+        if lam.shape[0] != self.n:
+            raise ValueError(f"expected {self.n} rows, got {lam.shape[0]}")
+        lam2 = lam.reshape(self.n, 1) if lam.dim() == 1 else lam
+        if lam2.dim() != 2:
+            raise ValueError("strengths must have shape (n,) or (n, nrhs)")
+        if lam2.stride(1) != 1:
+            lam2 = lam2.contiguous()
+        return lam2
+
+    def apply(self, lam: torch.Tensor, out: torch.Tensor | None = None, adjoint: bool = False,
+              path: str = "auto") -> torch.Tensor:
+        lam2 = self._check_lam(lam)
+        nrhs = lam2.shape[1]
+        if lam2.stride(0) != nrhs:
+            lam2 = lam2.contiguous()
+        if out is None:
+            out = torch.empty_like(lam2)
+        C.p2p_apply_path(self._plan, lam2, out, nrhs, nrhs, int(adjoint), PATHS[path], _stream())
+        return out.reshape(lam.shape)
+
+    def grad_points(self, lam: torch.Tensor, g: torch.Tensor) -> torch.Tensor:
+        lam2 = self._check_lam(lam).contiguous()
+        g2 = self._check_lam(g).contiguous()
+        grad = torch.empty((self.n, 3), dtype=torch.float32, device=lam.device)
+        C.p2p_grad_points(self._plan, lam2, g2, grad, lam2.shape[1], lam2.shape[1], _stream())
+        return grad
+
+    def close(self):
+        if getattr(self, "_plan", None):
+            C.p2p_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class P2PFunction(torch.autograd.Function):
+    """out = A(x) lam with gradients for lam (A^H g) and for x (radial-derivative kernel).
+
+    The box structure of the plan is held fixed: a coordinate gradient is the
+    derivative for a perturbation that moves no point across a box face.
+    """
+
+    @staticmethod
+    def forward(ctx, lam, points, plan: Plan):
+        ctx.plan = plan
+        ctx.save_for_backward(lam)
+        return plan.apply(lam)
+
+    @staticmethod
+    def backward(ctx, g):
+        (lam,) = ctx.saved_tensors
+        plan: Plan = ctx.plan
+        g = g.contiguous()
+        glam = plan.apply(g, adjoint=True) if ctx.needs_input_grad[0] else None
+        gx = plan.grad_points(lam, g) if ctx.needs_input_grad[1] else None
+        return glam, gx, None
+
+
+def p2p(lam: torch.Tensor, points: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Autograd entry: the plan must have been built from `points`."""
+    return P2PFunction.apply(lam, points, plan)
+
+
+def inv4pi() -> float:
+    return 1.0 / (4.0 * math.pi)

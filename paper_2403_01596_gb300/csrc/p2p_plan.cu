@@ -1,0 +1,650 @@
+// Leaf binning (Sec. 3.1, Morton order of Sec. 3.2), neighbour lists (Sec. 3.2,
+// 27-box 3D neighbourhood) and plan construction including the redundant
+// per-box packed layout (Sec. 3.3, eq. 6 - 8, collected on the device).
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "p2p_internal.cuh"
+
+namespace p2p_detail {
+
+static thread_local char g_last_error[512] = "";
+
+void set_cuda_error(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void set_message(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+}  // namespace p2p_detail
+
+using namespace p2p_detail;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t n, int per_block) { return (unsigned)((n + per_block - 1) / per_block); }
+
+// ------------------------------------------------------------------ binning --
+
+// cell = clamp(floor((double(x) - lo) / h), 0, ng - 1), with explicitly rounded
+// double operations so no contraction can change the result.
+__device__ __forceinline__ uint32_t cell_of(float x, double lo, double h, int ng) {
+    double t = __ddiv_rn(__dsub_rn((double)x, lo), h);
+    double f = floor(t);
+    if (f < 0.0) f = 0.0;
+    if (f > (double)(ng - 1)) f = (double)(ng - 1);
+    return (uint32_t)f;
+}
+
+__global__ void k_keys(const float* __restrict__ pts, int64_t n, double lo0, double lo1, double lo2, double h, int ng,
+                       uint64_t* __restrict__ keys, int32_t* __restrict__ vals, int32_t* __restrict__ bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
+        *bad = 1;
+        x = y = z = 0.f;
+    }
+    keys[i] = p2p_morton(cell_of(x, lo0, h, ng), cell_of(y, lo1, h, ng), cell_of(z, lo2, h, ng));
+    vals[i] = (int32_t)i;
+}
+
+__global__ void k_heads(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ head) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    head[s] = (s == 0 || keys[s] != keys[s - 1]) ? 1 : 0;
+}
+
+__global__ void k_rle(const uint64_t* __restrict__ keys, const int32_t* __restrict__ vals,
+                      const int32_t* __restrict__ head, const int32_t* __restrict__ ex, int64_t n,
+                      int32_t* __restrict__ perm, int32_t* __restrict__ point_box, int64_t* __restrict__ box_keys,
+                      int32_t* __restrict__ box_ptr) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int32_t id = ex[s] + head[s] - 1;
+    if (head[s]) {
+        box_keys[id] = (int64_t)keys[s];
+        box_ptr[id] = (int32_t)s;
+    }
+    const int32_t orig = vals[s];
+    perm[s] = orig;
+    point_box[orig] = id;
+    if (s == n - 1) box_ptr[id + 1] = (int32_t)n;
+}
+
+// --------------------------------------------------------------- neighbours --
+
+__device__ __forceinline__ int32_t find_key(const int64_t* __restrict__ keys, int32_t nb, int64_t key) {
+    int32_t lo = 0, hi = nb - 1;
+    while (lo <= hi) {
+        int32_t mid = lo + ((hi - lo) >> 1);
+        int64_t v = __ldg(keys + mid);
+        if (v == key) return mid;
+        if (v < key) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// Ascending bitonic sort of one int per lane across the warp.
+__device__ __forceinline__ int32_t warp_sort_asc(int32_t v, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            int32_t o = __shfl_xor_sync(P2P_FULL_MASK, v, j);
+            bool up = (lane & k) == 0;
+            bool lower = (lane & j) == 0;
+            v = (lower == up) ? min(v, o) : max(v, o);
+        }
+    }
+    return v;
+}
+
+// One warp per box; lane l < 27 probes the offset (l%3-1, (l/3)%3-1, l/9-1).
+template <bool FILL>
+__global__ void k_neighbors(const int64_t* __restrict__ box_keys, const int32_t* __restrict__ box_ptr, int32_t nb,
+                            int ng, int32_t* __restrict__ cnt, int32_t* __restrict__ src_cnt,
+                            const int32_t* __restrict__ nbr_ptr, int32_t* __restrict__ nbr_idx,
+                            int32_t* __restrict__ bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const uint64_t key = (uint64_t)box_keys[b];
+    const int cx = (int)p2p_compact3(key), cy = (int)p2p_compact3(key >> 1), cz = (int)p2p_compact3(key >> 2);
+    int32_t id = -1;
+    if (lane < 27) {
+        int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+        if (x >= 0 && y >= 0 && z >= 0 && x < ng && y < ng && z < ng)
+            id = find_key(box_keys, nb, (int64_t)p2p_morton(x, y, z));
+    }
+    const unsigned found = __ballot_sync(P2P_FULL_MASK, id >= 0);
+    if (!FILL) {
+        int s = id >= 0 ? box_ptr[id + 1] - box_ptr[id] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(P2P_FULL_MASK, s, o);
+        if (lane == 0) {
+            cnt[b] = __popc(found);
+            src_cnt[b] = s;
+            if (b > 0 && box_keys[b - 1] >= box_keys[b]) *bad = 1;  // keys must strictly ascend
+            if (!((found >> 13) & 1u)) *bad = 1;                     // a box must find itself
+        }
+    } else {
+        int32_t v = warp_sort_asc(id >= 0 ? id : INT32_MAX, lane);
+        if (lane < __popc(found)) nbr_idx[nbr_ptr[b] + lane] = v;
+    }
+}
+
+__global__ void k_sum_i32(const int32_t* __restrict__ v, int64_t n, unsigned long long* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    long long s = i < n ? (long long)v[i] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(P2P_FULL_MASK, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, (unsigned long long)s);
+}
+
+// -------------------------------------------------------------------- plans --
+
+__global__ void k_gather_xyz(const float* __restrict__ pts, const int32_t* __restrict__ perm, int64_t n,
+                             float4* __restrict__ xs) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int64_t j = perm[s];
+    xs[s] = make_float4(pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], 0.f);
+}
+
+// Per box: S_b, position of the own box inside the concatenated neighbourhood,
+// work-item count ceil(S_b / chunk) and padded packed size.  Validates the CSR.
+__global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ nbr_ptr,
+                           const int32_t* __restrict__ nbr_idx, int32_t nb, int64_t nnz, int chunk,
+                           int32_t* __restrict__ box_src, int32_t* __restrict__ box_self,
+                           int32_t* __restrict__ n_chunks, int32_t* __restrict__ padded, int32_t* __restrict__ maxes,
+                           unsigned int* __restrict__ status) {
+    int32_t b = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (b >= nb) return;
+    int32_t e0 = nbr_ptr[b], e1 = nbr_ptr[b + 1];
+    int64_t s = 0, self = -1;
+    bool ok = e0 >= 0 && e1 >= e0 && e1 <= nnz && e1 - e0 <= 27;
+    if (ok) {
+        for (int32_t e = e0; e < e1; ++e) {
+            int32_t c = nbr_idx[e];
+            if (c < 0 || c >= nb || (e > e0 && c <= nbr_idx[e - 1])) {
+                ok = false;
+                break;
+            }
+            if (c == b) self = s;
+            s += box_ptr[c + 1] - box_ptr[c];
+        }
+    }
+    int32_t own = box_ptr[b + 1] - box_ptr[b];
+    if (!ok || self < 0 || own <= 0 || s > INT32_MAX - 4) {
+        atomicOr(status, P2P_DEV_BAD_INPUT);
+        s = 0;
+        self = 0;
+    }
+    box_src[b] = (int32_t)s;
+    box_self[b] = (int32_t)self;
+    int32_t c = (int32_t)((s + chunk - 1) / chunk);
+    n_chunks[b] = c;
+    padded[b] = (int32_t)((s + 3) & ~3ll);
+    atomicMax(&maxes[0], c);
+    atomicMax(&maxes[1], own);
+}
+
+__global__ void k_items(const int32_t* __restrict__ n_chunks, const int32_t* __restrict__ item_off, int32_t nb,
+                        int chunk, int4* __restrict__ items) {
+    int32_t b = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (b >= nb) return;
+    int32_t c = n_chunks[b], o = item_off[b];
+    for (int32_t i = 0; i < c; ++i) items[o + i] = make_int4(b, i * chunk, 0, 0);
+}
+
+// One warp per box: copy the neighbourhood's sources into the box's packed tile.
+__global__ void k_pack(const float4* __restrict__ xs, const int32_t* __restrict__ perm,
+                       const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ nbr_ptr,
+                       const int32_t* __restrict__ nbr_idx, const int32_t* __restrict__ pk_off, int32_t nb,
+                       float4* __restrict__ pk_xyz, int32_t* __restrict__ pk_src) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const int32_t e0 = nbr_ptr[b], ne = nbr_ptr[b + 1] - e0;
+    int32_t start = 0, len = 0;
+    if (lane < ne) {
+        int32_t c = nbr_idx[e0 + lane];
+        start = box_ptr[c];
+        len = box_ptr[c + 1] - start;
+    }
+    int32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(P2P_FULL_MASK, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int32_t excl = incl - len;
+    const int32_t total = __shfl_sync(P2P_FULL_MASK, incl, 31);
+    const int64_t base = pk_off[b];
+    const int32_t padded = pk_off[b + 1] - pk_off[b];
+    for (int32_t p0 = 0; p0 < padded; p0 += 32) {
+        const int32_t p = p0 + lane;
+        int32_t seg = 0;
+        for (int e = 0; e < ne; ++e) {
+            int32_t ex = __shfl_sync(P2P_FULL_MASK, excl, e);
+            if (p >= ex) seg = e;
+        }
+        const int32_t s0 = __shfl_sync(P2P_FULL_MASK, start, seg);
+        const int32_t x0 = __shfl_sync(P2P_FULL_MASK, excl, seg);
+        if (p < total) {
+            const int32_t j = s0 + (p - x0);
+            pk_xyz[base + p] = xs[j];
+            pk_src[base + p] = perm[j];
+        } else if (p < padded) {
+            pk_xyz[base + p] = make_float4(0.f, 0.f, 0.f, 0.f);
+            pk_src[base + p] = -1;
+        }
+    }
+}
+
+// Pairs of box b: n_b * S_b minus the pairs inside b with identical coordinates.
+__global__ void k_pair_count(const float4* __restrict__ xs, const int32_t* __restrict__ box_ptr,
+                             const int32_t* __restrict__ box_src, int32_t nb, unsigned long long* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const int32_t t0 = box_ptr[b], t1 = box_ptr[b + 1];
+    long long dup = 0;
+    for (int32_t i = t0 + lane; i < t1; i += 32) {
+        float4 a = xs[i];
+        for (int32_t j = t0; j < t1; ++j) {
+            float4 c = xs[j];
+            dup += (a.x == c.x && a.y == c.y && a.z == c.z) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dup += __shfl_xor_sync(P2P_FULL_MASK, dup, o);
+    if (lane == 0) {
+        long long p = (long long)(t1 - t0) * (long long)box_src[b] - dup;
+        atomicAdd(out, (unsigned long long)p);
+    }
+}
+
+int ceil_log2(int v) {
+    int b = 0;
+    while ((1 << b) < v) ++b;
+    return b;
+}
+
+struct BinLayout {
+    uint64_t *keys, *keys_alt;
+    int32_t *vals, *vals_alt, *head, *ex, *small;
+    void *radix_ws, *scan_ws;
+    size_t bytes;
+};
+
+BinLayout bin_layout(int64_t n, void* work) {
+    Carver c{static_cast<char*>(work), 0, (size_t)-1};
+    BinLayout L;
+    size_t m = (size_t)(n > 0 ? n : 1);
+    L.keys = c.take<uint64_t>(m);
+    L.keys_alt = c.take<uint64_t>(m);
+    L.vals = c.take<int32_t>(m);
+    L.vals_alt = c.take<int32_t>(m);
+    L.head = c.take<int32_t>(m);
+    L.ex = c.take<int32_t>(m);
+    L.small = c.take<int32_t>(4);
+    L.radix_ws = c.take<char>(radix_workspace_bytes(n));
+    L.scan_ws = c.take<char>(scan_workspace_bytes(n));
+    L.bytes = align_up(c.off, 256);
+    return L;
+}
+
+struct NbrLayout {
+    int32_t *cnt, *src_cnt, *bad;
+    unsigned long long* sum;
+    void* scan_ws;
+    size_t bytes;
+};
+
+NbrLayout nbr_layout(int32_t nb, void* work) {
+    Carver c{static_cast<char*>(work), 0, (size_t)-1};
+    NbrLayout L;
+    size_t m = (size_t)(nb > 0 ? nb : 1);
+    L.cnt = c.take<int32_t>(m);
+    L.src_cnt = c.take<int32_t>(m);
+    L.bad = c.take<int32_t>(2);
+    L.sum = c.take<unsigned long long>(1);
+    L.scan_ws = c.take<char>(scan_workspace_bytes(nb));
+    L.bytes = align_up(c.off, 256);
+    return L;
+}
+
+bool tuning_valid(const p2p_tuning& t) {
+    return t.chunk >= 32 && t.chunk <= 1024 && t.chunk % 32 == 0 && t.warps_per_cta >= 1 && t.warps_per_cta <= 16 &&
+           t.target_group >= 32 && t.target_group <= 128 && t.target_group % 32 == 0;
+}
+
+p2p_tuning resolve_tuning(const p2p_tuning* t) {
+    p2p_tuning r{128, 8, 128, 0};
+    if (t) {
+        if (t->chunk) r.chunk = t->chunk;
+        if (t->warps_per_cta) r.warps_per_cta = t->warps_per_cta;
+        if (t->target_group) r.target_group = t->target_group;
+    }
+    return r;
+}
+
+struct PlanLayout {
+    p2p_plan p;  // pointers only
+    int32_t *n_chunks, *item_off, *padded, *maxes, *small;
+    void* scan_ws;
+    size_t bytes;
+};
+
+PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, p2p_layout layout, int32_t max_nrhs,
+                       const p2p_tuning& t, void* ws) {
+    Carver c{static_cast<char*>(ws), 0, (size_t)-1};
+    PlanLayout L;
+    memset(&L.p, 0, sizeof(L.p));
+    size_t m = (size_t)(n > 0 ? n : 1), mb = (size_t)(nb > 0 ? nb : 1);
+    const size_t max_items = (size_t)(sources / t.chunk) + mb + 1;
+    const size_t packed_bound = layout == P2P_LAYOUT_REDUNDANT ? (size_t)sources + 3 * mb + 4 : 0;
+    L.p.status = c.take<unsigned int>(4);
+    L.p.scratch64 = c.take<long long>(4);
+    L.p.xs = c.take<float4>(m);
+    L.p.box_src = c.take<int32_t>(mb);
+    L.p.box_self = c.take<int32_t>(mb);
+    L.p.items = c.take<int4>(max_items);
+    L.p.pk_off = c.take<int32_t>(mb + 1);
+    L.p.pk_xyz = c.take<float4>(packed_bound ? packed_bound : 1);
+    L.p.pk_src = c.take<int32_t>(packed_bound ? packed_bound : 1);
+    const size_t lam_rows = m > packed_bound ? m : packed_bound;
+    L.p.lam_buf = c.take<float2>(lam_rows * (size_t)max_nrhs);
+    L.p.g_buf = c.take<float2>(m * (size_t)max_nrhs);
+    L.n_chunks = c.take<int32_t>(mb);
+    L.item_off = c.take<int32_t>(mb + 1);
+    L.padded = c.take<int32_t>(mb);
+    L.maxes = c.take<int32_t>(4);
+    L.small = c.take<int32_t>(4);
+    L.scan_ws = c.take<char>(scan_workspace_bytes(nb));
+    L.bytes = align_up(c.off, 256);
+    return L;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI ==
+
+extern "C" {
+
+P2P_API int32_t p2p_version(void) { return 100; }
+
+P2P_API const char* p2p_status_string(p2p_status s) {
+    switch (s) {
+        case P2P_OK: return "ok";
+        case P2P_ERR_INVALID: return "invalid argument or input";
+        case P2P_ERR_WORKSPACE: return "workspace too small";
+        case P2P_ERR_CUDA: return "CUDA error";
+        case P2P_ERR_TIMEOUT: return "device-side wait timed out";
+        case P2P_ERR_UNSUPPORTED: return "unsupported";
+        case P2P_ERR_ALLOC: return "host allocation failed";
+    }
+    return "unknown status";
+}
+
+P2P_API const char* p2p_last_error_string(void) { return g_last_error; }
+
+P2P_API p2p_status p2p_bin_workspace_size(int64_t n, size_t* bytes) {
+    if (!bytes || n < 0 || n >= INT32_MAX) return P2P_ERR_INVALID;
+    *bytes = bin_layout(n, nullptr).bytes;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_bin_points(const float* pts, int64_t n, const double lo[3], double h, int32_t ng,
+                                  int32_t* perm, int32_t* point_box, int64_t* box_keys, int32_t* box_ptr,
+                                  int32_t* num_boxes, void* work, size_t work_bytes, p2p_stream_t stream) {
+    if (n < 0 || n >= INT32_MAX || !lo || !num_boxes || !box_ptr || !(h > 0.0) || !isfinite(h) || ng < 1 ||
+        ng > (1 << 21))
+        return P2P_ERR_INVALID;
+    if (!isfinite(lo[0]) || !isfinite(lo[1]) || !isfinite(lo[2])) return P2P_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    *num_boxes = 0;
+    if (n == 0) {
+        P2P_TRY_CUDA(cudaMemsetAsync(box_ptr, 0, sizeof(int32_t), s), "p2p_bin_points");
+        P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_bin_points");
+        return P2P_OK;
+    }
+    if (!pts || !perm || !point_box || !box_keys || !work) return P2P_ERR_INVALID;
+    if (((uintptr_t)pts & 3) || ((uintptr_t)work & 255)) return P2P_ERR_INVALID;
+    BinLayout L = bin_layout(n, work);
+    if (work_bytes < L.bytes) return P2P_ERR_WORKSPACE;
+
+    P2P_TRY_CUDA(cudaMemsetAsync(L.small, 0, 4 * sizeof(int32_t), s), "p2p_bin_points");
+    k_keys<<<blocks_for(n, kThreads), kThreads, 0, s>>>(pts, n, lo[0], lo[1], lo[2], h, ng, L.keys, L.vals, L.small);
+    P2P_CHECK_LAUNCH("p2p_bin_points/keys");
+    bool in_alt = false;
+    P2P_TRY_CUDA(radix_sort_pairs(L.keys, L.vals, L.keys_alt, L.vals_alt, n, 3 * ceil_log2(ng), L.radix_ws, s, &in_alt),
+                 "p2p_bin_points/sort");
+    const uint64_t* ks = in_alt ? L.keys_alt : L.keys;
+    const int32_t* vs = in_alt ? L.vals_alt : L.vals;
+    k_heads<<<blocks_for(n, kThreads), kThreads, 0, s>>>(ks, n, L.head);
+    P2P_CHECK_LAUNCH("p2p_bin_points/heads");
+    P2P_TRY_CUDA(scan_exclusive_i32(L.head, L.ex, n, L.small + 1, L.scan_ws, s), "p2p_bin_points/scan");
+    k_rle<<<blocks_for(n, kThreads), kThreads, 0, s>>>(ks, vs, L.head, L.ex, n, perm, point_box, box_keys, box_ptr);
+    P2P_CHECK_LAUNCH("p2p_bin_points/rle");
+    int32_t host[2] = {0, 0};
+    P2P_TRY_CUDA(cudaMemcpyAsync(host, L.small, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_bin_points");
+    P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_bin_points");
+    if (host[0]) return P2P_ERR_INVALID;
+    *num_boxes = host[1];  // total of the head flags = number of non-empty boxes
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_neighbors_workspace_size(int32_t num_boxes, size_t* bytes) {
+    if (!bytes || num_boxes < 0) return P2P_ERR_INVALID;
+    *bytes = nbr_layout(num_boxes, nullptr).bytes;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_build_neighbors(const int64_t* box_keys, const int32_t* box_ptr, int32_t num_boxes,
+                                       int32_t ng, int32_t* nbr_ptr, int32_t* nbr_idx, int64_t* nnz,
+                                       int64_t* sources, void* work, size_t work_bytes, p2p_stream_t stream) {
+    if (num_boxes < 0 || ng < 1 || ng > (1 << 21) || !nbr_ptr || !nnz || !sources) return P2P_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    *nnz = 0;
+    *sources = 0;
+    if (num_boxes == 0) {
+        P2P_TRY_CUDA(cudaMemsetAsync(nbr_ptr, 0, sizeof(int32_t), s), "p2p_build_neighbors");
+        P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_build_neighbors");
+        return P2P_OK;
+    }
+    if (!box_keys || !box_ptr || !nbr_idx || !work || ((uintptr_t)work & 255)) return P2P_ERR_INVALID;
+    if ((int64_t)num_boxes * 27 >= INT32_MAX) return P2P_ERR_UNSUPPORTED;
+    NbrLayout L = nbr_layout(num_boxes, work);
+    if (work_bytes < L.bytes) return P2P_ERR_WORKSPACE;
+    P2P_TRY_CUDA(cudaMemsetAsync(L.bad, 0, 2 * sizeof(int32_t), s), "p2p_build_neighbors");
+    P2P_TRY_CUDA(cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long), s), "p2p_build_neighbors");
+    const unsigned wblocks = blocks_for((int64_t)num_boxes * 32, kThreads);
+    k_neighbors<false><<<wblocks, kThreads, 0, s>>>(box_keys, box_ptr, num_boxes, ng, L.cnt, L.src_cnt, nullptr,
+                                                    nullptr, L.bad);
+    P2P_CHECK_LAUNCH("p2p_build_neighbors/count");
+    P2P_TRY_CUDA(scan_exclusive_i32(L.cnt, nbr_ptr, num_boxes, nbr_ptr + num_boxes, L.scan_ws, s),
+                 "p2p_build_neighbors/scan");
+    k_neighbors<true><<<wblocks, kThreads, 0, s>>>(box_keys, box_ptr, num_boxes, ng, nullptr, nullptr, nbr_ptr,
+                                                   nbr_idx, L.bad);
+    P2P_CHECK_LAUNCH("p2p_build_neighbors/fill");
+    k_sum_i32<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(L.src_cnt, num_boxes, L.sum);
+    P2P_CHECK_LAUNCH("p2p_build_neighbors/sum");
+    int32_t bad = 0, total = 0;
+    unsigned long long src = 0;
+    P2P_TRY_CUDA(cudaMemcpyAsync(&bad, L.bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_build_neighbors");
+    P2P_TRY_CUDA(cudaMemcpyAsync(&total, nbr_ptr + num_boxes, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                 "p2p_build_neighbors");
+    P2P_TRY_CUDA(cudaMemcpyAsync(&src, L.sum, sizeof(src), cudaMemcpyDeviceToHost, s), "p2p_build_neighbors");
+    P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_build_neighbors");
+    if (bad) return P2P_ERR_INVALID;
+    *nnz = total;
+    *sources = (int64_t)src;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_plan_workspace_size(int64_t n, int32_t num_boxes, int64_t nnz, int64_t sources,
+                                           p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
+                                           size_t* bytes) {
+    (void)nnz;
+    if (!bytes || n < 0 || n >= INT32_MAX || num_boxes < 0 || num_boxes > n || sources < 0 ||
+        sources >= INT32_MAX || max_nrhs < 1 || max_nrhs > 256 ||
+        (layout != P2P_LAYOUT_INDEXED && layout != P2P_LAYOUT_REDUNDANT))
+        return P2P_ERR_INVALID;
+    p2p_tuning t = resolve_tuning(tuning);
+    if (!tuning_valid(t)) return P2P_ERR_INVALID;
+    *bytes = plan_layout(n, num_boxes, sources, layout, max_nrhs, t, nullptr).bytes;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n, const int32_t* perm,
+                                   const int32_t* box_ptr, int32_t num_boxes, const int32_t* nbr_ptr,
+                                   const int32_t* nbr_idx, int64_t nnz, int64_t sources, p2p_kernel kernel, float k,
+                                   p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning, void* workspace,
+                                   size_t workspace_bytes, p2p_stream_t stream) {
+    if (!plan) return P2P_ERR_INVALID;
+    *plan = nullptr;
+    size_t need = 0;
+    p2p_status st = p2p_plan_workspace_size(n, num_boxes, nnz, sources, layout, max_nrhs, tuning, &need);
+    if (st != P2P_OK) return st;
+    if (kernel != P2P_HELMHOLTZ && kernel != P2P_LAPLACE) return P2P_ERR_INVALID;
+    if (!isfinite(k)) return P2P_ERR_INVALID;
+    if ((n > 0 && num_boxes < 1) || (n == 0 && num_boxes != 0)) return P2P_ERR_INVALID;
+    if (nnz < num_boxes || nnz > 27ll * num_boxes) return P2P_ERR_INVALID;
+    if (n > 0 && (!pts || !perm || !box_ptr || !nbr_ptr || !nbr_idx)) return P2P_ERR_INVALID;
+    if (!workspace || ((uintptr_t)workspace & 255) || ((uintptr_t)pts & 3)) return P2P_ERR_INVALID;
+    if (workspace_bytes < need) return P2P_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    p2p_tuning t = resolve_tuning(tuning);
+    PlanLayout L = plan_layout(n, num_boxes, sources, layout, max_nrhs, t, workspace);
+    p2p_plan* p = (p2p_plan*)malloc(sizeof(p2p_plan));
+    if (!p) return P2P_ERR_ALLOC;
+    *p = L.p;
+    p->n = n;
+    p->nb = num_boxes;
+    p->nnz = nnz;
+    p->sources = sources;
+    p->kernel = kernel;
+    p->k = kernel == P2P_LAPLACE ? 0.f : k;
+    p->layout = layout;
+    p->max_nrhs = max_nrhs;
+    p->tune = t;
+    p->pts = pts;
+    p->perm = perm;
+    p->box_ptr = box_ptr;
+    p->nbr_ptr = nbr_ptr;
+    p->nbr_idx = nbr_idx;
+    p->n_items = 0;
+    p->max_chunks = 0;
+    p->max_box = 0;
+    p->packed = 0;
+#define FAIL_CUDA(expr, where)                 \
+    do {                                       \
+        cudaError_t e_ = (expr);               \
+        if (e_ != cudaSuccess) {               \
+            set_cuda_error(e_, where);         \
+            free(p);                           \
+            return P2P_ERR_CUDA;               \
+        }                                      \
+    } while (0)
+    FAIL_CUDA(cudaMemsetAsync(p->status, 0, 4 * sizeof(unsigned int), s), "p2p_plan_create");
+    if (n == 0) {
+        FAIL_CUDA(cudaStreamSynchronize(s), "p2p_plan_create");
+        *plan = p;
+        return P2P_OK;
+    }
+    FAIL_CUDA(cudaMemsetAsync(L.maxes, 0, 4 * sizeof(int32_t), s), "p2p_plan_create");
+    k_gather_xyz<<<blocks_for(n, kThreads), kThreads, 0, s>>>(pts, perm, n, p->xs);
+    FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/gather");
+    k_box_info<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(box_ptr, nbr_ptr, nbr_idx, num_boxes, nnz,
+                                                                     t.chunk, p->box_src, p->box_self, L.n_chunks,
+                                                                     L.padded, L.maxes, p->status);
+    FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/box_info");
+    FAIL_CUDA(scan_exclusive_i32(L.n_chunks, L.item_off, num_boxes, L.small, L.scan_ws, s), "p2p_plan_create/scan");
+    k_items<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(L.n_chunks, L.item_off, num_boxes, t.chunk,
+                                                                 p->items);
+    FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/items");
+    if (layout == P2P_LAYOUT_REDUNDANT) {
+        FAIL_CUDA(scan_exclusive_i32(L.padded, p->pk_off, num_boxes, p->pk_off + num_boxes, L.scan_ws, s),
+                  "p2p_plan_create/scan_packed");
+        k_pack<<<blocks_for((int64_t)num_boxes * 32, kThreads), kThreads, 0, s>>>(
+            p->xs, perm, box_ptr, nbr_ptr, nbr_idx, p->pk_off, num_boxes, p->pk_xyz, p->pk_src);
+        FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/pack");
+    }
+    int32_t host[4] = {0, 0, 0, 0};
+    unsigned int status = 0;
+    int32_t packed = 0;
+    FAIL_CUDA(cudaMemcpyAsync(host, L.maxes, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
+    FAIL_CUDA(cudaMemcpyAsync(host + 2, L.small, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
+    FAIL_CUDA(cudaMemcpyAsync(&status, p->status, sizeof(status), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
+    if (layout == P2P_LAYOUT_REDUNDANT)
+        FAIL_CUDA(cudaMemcpyAsync(&packed, p->pk_off + num_boxes, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                  "p2p_plan_create");
+    FAIL_CUDA(cudaStreamSynchronize(s), "p2p_plan_create");
+#undef FAIL_CUDA
+    if (status) {
+        free(p);
+        return P2P_ERR_INVALID;
+    }
+    p->max_chunks = host[0];
+    p->max_box = host[1];
+    p->n_items = host[2];
+    p->packed = packed;
+    *plan = p;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_plan_destroy(p2p_plan* plan) {
+    free(plan);
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_plan_info(const p2p_plan* plan, int64_t* n, int32_t* num_boxes, int64_t* sources,
+                                 int64_t* work_items, p2p_layout* layout, p2p_tuning* tuning) {
+    if (!plan) return P2P_ERR_INVALID;
+    if (n) *n = plan->n;
+    if (num_boxes) *num_boxes = plan->nb;
+    if (sources) *sources = plan->sources;
+    if (work_items) *work_items = plan->n_items;
+    if (layout) *layout = plan->layout;
+    if (tuning) *tuning = plan->tune;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_plan_pair_count(const p2p_plan* plan, int64_t* pairs, p2p_stream_t stream) {
+    if (!plan || !pairs) return P2P_ERR_INVALID;
+    *pairs = 0;
+    if (plan->n == 0) return P2P_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    P2P_TRY_CUDA(cudaMemsetAsync(plan->scratch64, 0, sizeof(long long), s), "p2p_plan_pair_count");
+    k_pair_count<<<blocks_for((int64_t)plan->nb * 32, kThreads), kThreads, 0, s>>>(
+        plan->xs, plan->box_ptr, plan->box_src, plan->nb, (unsigned long long*)plan->scratch64);
+    P2P_CHECK_LAUNCH("p2p_plan_pair_count");
+    long long v = 0;
+    P2P_TRY_CUDA(cudaMemcpyAsync(&v, plan->scratch64, sizeof(v), cudaMemcpyDeviceToHost, s), "p2p_plan_pair_count");
+    P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_plan_pair_count");
+    *pairs = v;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_last_async_status(const p2p_plan* plan, p2p_stream_t stream) {
+    if (!plan) return P2P_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int v = 0;
+    P2P_TRY_CUDA(cudaMemcpyAsync(&v, plan->status, sizeof(v), cudaMemcpyDeviceToHost, s), "p2p_last_async_status");
+    P2P_TRY_CUDA(cudaMemsetAsync(plan->status, 0, sizeof(unsigned int), s), "p2p_last_async_status");
+    P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_last_async_status");
+    if (v & P2P_DEV_TIMEOUT) return P2P_ERR_TIMEOUT;
+    if (v & P2P_DEV_BAD_INPUT) return P2P_ERR_INVALID;
+    if (v & P2P_DEV_TC_FAULTED) return P2P_ERR_UNSUPPORTED;
+    return P2P_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+"""GPU parity of the CUDA path against the FP64 oracle (call through the C ABI).
+
+Tolerances (FP32 kernel vs FP64 oracle): relative L2 error per right-hand
+side <= 1e-5 for potentials; box ids, permutation, box pointers and neighbour
+lists bit-exact.  The coordinate gradient is compared at relative L2 <= 1e-4
+(its terms scale like 1/r^2, one more power of the close-pair dynamic range).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_01596_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_01596_gb300 import api
+    return api
+
+
+def rel_l2(x, ref):
+    x = np.asarray(x).reshape(ref.shape[0], -1)
+    ref = np.asarray(ref).reshape(ref.shape[0], -1)
+    return np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+def _plan(api, wl, kernel="helmholtz", layout="indexed", max_nrhs=1, tuning=None, k=None):
+    pts = torch.from_numpy(wl.points).cuda()
+    return api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k if k is None else k, kernel=kernel, layout=layout,
+                    max_nrhs=max_nrhs, tuning=tuning)
+
+
+def _small_sphere(n=40000, ng=40, seed=5):
+    p = W.unit_sphere(n, seed)
+    return W.Workload(f"sphere{n}", p, (-1.0, -1.0, -1.0), 2.0 / ng, ng, 2 * np.pi / (4 * 2.0 / ng), seed)
+
+
+def _clustered(n=30000, seed=12):
+    p = W.cylinder_plates(n, seed)
+    ng = 48
+    h = 2.6 / ng
+    return W.Workload("clustered", p, (-1.3, -1.3, -1.3), h, ng, 2 * np.pi * 0.2 / h, seed)
+
+
+STRUCT_CASES = {
+    "cube8": lambda: W.cube_dense(),
+    "sphere40": lambda: _small_sphere(),
+    "clustered": lambda: _clustered(),
+    "ellipsoid": lambda: W.Workload("ell", W.ellipsoid_211(20000, 7), (-2.0, -2.0, -2.0), 4.0 / 37, 37, 10.0, 7),
+}
+
+
+@pytest.mark.parametrize("case", sorted(STRUCT_CASES))
+def test_binning_and_neighbors_bit_exact(case):
+    api = _cuda()
+    wl = STRUCT_CASES[case]()
+    st = api.BoxStructure(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng)
+    ref = oracle.bin_points(wl.points, wl.lo, wl.h, wl.ng)
+    assert st.num_boxes == ref["num_boxes"]
+    np.testing.assert_array_equal(st.perm.cpu().numpy()[:wl.n], ref["perm"])
+    np.testing.assert_array_equal(st.point_box.cpu().numpy()[:wl.n], ref["point_box"])
+    np.testing.assert_array_equal(st.box_keys.cpu().numpy(), ref["box_keys"])
+    np.testing.assert_array_equal(st.box_ptr.cpu().numpy(), ref["box_ptr"])
+    nptr, nidx = oracle.neighbors(ref["box_keys"], wl.ng)
+    np.testing.assert_array_equal(st.nbr_ptr.cpu().numpy(), nptr)
+    np.testing.assert_array_equal(st.nbr_idx.cpu().numpy()[:st.nnz], nidx)
+    sizes = np.diff(ref["box_ptr"])
+    assert st.sources == int(sum(sizes[nidx[nptr[b]:nptr[b + 1]]].sum() for b in range(ref["num_boxes"])))
+
+
+@pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
+@pytest.mark.parametrize("layout", ["indexed", "redundant"])
+def test_apply_dense_cube(kernel, layout):
+    """Uniform cube, 8^3 boxes (~64 points per box, ~1350 sources per box: several chunks)."""
+    api = _cuda()
+    wl = W.cube_dense()
+    lam = W.strengths(wl.n, 1, wl.seed)
+    plan = _plan(api, wl, kernel, layout)
+    out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
+    kern = oracle.HELMHOLTZ if kernel == "helmholtz" else oracle.LAPLACE
+    ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k if kernel == "helmholtz" else 0.0, kernel=kern)
+    err = rel_l2(out, ref)
+    assert err.max() <= TOL, err
+    assert plan.async_status() == 0
+    assert plan.pair_count() == oracle.pair_count(wl.points, wl.lo, wl.h, wl.ng)
+
+
+@pytest.mark.parametrize("layout", ["indexed", "redundant"])
+@pytest.mark.parametrize("case", ["sphere40", "clustered", "ellipsoid"])
+def test_apply_surfaces(layout, case):
+    api = _cuda()
+    wl = STRUCT_CASES[case]()
+    lam = W.strengths(wl.n, 1, wl.seed)
+    plan = _plan(api, wl, "helmholtz", layout)
+    out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
+    ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
+    assert rel_l2(out, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("tuning", [{"chunk": 32, "warps_per_cta": 4, "target_group": 32},
+                                    {"chunk": 64, "warps_per_cta": 1, "target_group": 64},
+                                    {"chunk": 256, "warps_per_cta": 16, "target_group": 128},
+                                    {"chunk": 1024, "warps_per_cta": 2, "target_group": 96}])
+def test_apply_tunings(tuning):
+    api = _cuda()
+    wl = _clustered(12000, 13)
+    lam = W.strengths(wl.n, 1, 3)
+    ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
+    for layout in ("indexed", "redundant"):
+        plan = _plan(api, wl, "helmholtz", layout, tuning=tuning)
+        out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
+        assert rel_l2(out, ref).max() <= TOL, (layout, tuning)
+
+
+@pytest.mark.parametrize("path", ["fp32_per_rhs", "fp32_shared"])
+@pytest.mark.parametrize("nrhs", [2, 3, 5, 8])
+def test_multi_rhs(path, nrhs):
+    api = _cuda()
+    wl = _small_sphere(20000, 30, 8)
+    lam = W.strengths(wl.n, nrhs, 8)
+    ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
+    for layout in ("indexed", "redundant"):
+        plan = _plan(api, wl, "helmholtz", layout, max_nrhs=nrhs)
+        out = plan.apply(torch.from_numpy(lam).cuda(), path=path).cpu().numpy()
+        err = rel_l2(out, ref)
+        assert err.shape == (nrhs,) and err.max() <= TOL, err
+
+
+def test_adjoint():
+    api = _cuda()
+    wl = _small_sphere(30000, 36, 9)
+    g = W.strengths(wl.n, 2, 9)
+    for layout in ("indexed", "redundant"):
+        plan = _plan(api, wl, "helmholtz", layout, max_nrhs=2)
+        out = plan.apply(torch.from_numpy(g).cuda(), adjoint=True).cpu().numpy()
+        ref = oracle.p2p(wl.points, g, wl.lo, wl.h, wl.ng, wl.k, adjoint=True)
+        assert rel_l2(out, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
+def test_grad_points(kernel):
+    api = _cuda()
+    wl = W.sphere_grad(1 << 15, 3)
+    wl = W.Workload(wl.name, wl.points, wl.lo, 2.0 / 22, 22, 2 * np.pi * 3, 3)
+    lam = W.strengths(wl.n, 1, 3)
+    g = W.strengths(wl.n, 1, 4)
+    plan = _plan(api, wl, kernel, "indexed")
+    kern = oracle.HELMHOLTZ if kernel == "helmholtz" else oracle.LAPLACE
+    k = wl.k if kernel == "helmholtz" else 0.0
+    gx = plan.grad_points(torch.from_numpy(lam).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
+    ref = oracle.grad_points(wl.points, lam, g, wl.lo, wl.h, wl.ng, k, kernel=kern)
+    err = np.linalg.norm(gx - ref) / np.linalg.norm(ref)
+    assert err <= 1e-4, err
+
+
+def test_autograd_function():
+    api = _cuda()
+    wl = _small_sphere(8000, 20, 14)
+    pts = torch.from_numpy(wl.points).cuda().requires_grad_(True)
+    plan = api.Plan(pts.detach(), wl.lo, wl.h, wl.ng, wl.k)
+    lam = torch.from_numpy(W.strengths(wl.n, 1, 14)).cuda().requires_grad_(True)
+    b = torch.from_numpy(W.strengths(wl.n, 1, 15)).cuda()
+    out = api.p2p(lam, pts, plan)
+    loss = (out - b).abs().pow(2).sum()
+    loss.backward()
+    g = 2 * (out.detach() - b)
+    ref_lam = oracle.p2p(wl.points, g.cpu().numpy(), wl.lo, wl.h, wl.ng, wl.k, adjoint=True)
+    assert rel_l2(lam.grad.cpu().numpy(), ref_lam).max() <= TOL
+    ref_x = oracle.grad_points(wl.points, lam.detach().cpu().numpy(), g.cpu().numpy(), wl.lo, wl.h, wl.ng, wl.k)
+    assert np.linalg.norm(pts.grad.cpu().numpy() - ref_x) / np.linalg.norm(ref_x) <= 1e-4
+
+
+def test_edge_cases():
+    api = _cuda()
+    # one point: no pairs, zero output
+    one = W.Workload("one", np.array([[0.3, 0.3, 0.3]], np.float32), (0, 0, 0), 0.5, 2, 3.0, 0)
+    plan = _plan(api, one)
+    out = plan.apply(torch.ones(1, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    assert out[0] == 0
+    # empty point set
+    empty = W.Workload("empty", np.zeros((0, 3), np.float32), (0, 0, 0), 0.5, 2, 3.0, 0)
+    plan = _plan(api, empty)
+    assert plan.apply(torch.zeros(0, dtype=torch.complex64, device="cuda")).numel() == 0
+    # duplicates, points outside the grid, one dense box of 700 points (> target group, > chunk)
+    rng = np.random.default_rng(4)
+    p = np.concatenate([rng.random((700, 3)) * 0.1 + 0.45, rng.random((300, 3)) * 1.4 - 0.2])
+    p = p.astype(np.float32)
+    p[10] = p[11]
+    p[20] = p[21] = p[22]
+    wl = W.Workload("edge", p, (0, 0, 0), 0.125, 8, 9.0, 0)
+    lam = W.strengths(len(p), 1, 4)
+    ref = oracle.p2p(p, lam, wl.lo, wl.h, wl.ng, wl.k)
+    for layout in ("indexed", "redundant"):
+        for tuning in (None, {"chunk": 32, "target_group": 32}):
+            plan = _plan(api, wl, "helmholtz", layout, tuning=tuning)
+            out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
+            assert rel_l2(out, ref).max() <= TOL
+    assert plan.pair_count() == oracle.pair_count(p, wl.lo, wl.h, wl.ng)
+    # ng = 1: a single box, the dense all-pairs case
+    wl1 = W.Workload("single", W.uniform_cube(3000, 5), (0, 0, 0), 1.0, 1, 6.0, 0)
+    lam1 = W.strengths(3000, 1, 5)
+    out = _plan(api, wl1).apply(torch.from_numpy(lam1).cuda()).cpu().numpy()
+    assert rel_l2(out, oracle.p2p(wl1.points, lam1, (0, 0, 0), 1.0, 1, 6.0)).max() <= TOL
+
+
+def test_invalid_points_rejected():
+    api = _cuda()
+    from paper_2403_01596_gb300._capi import P2PError
+    p = W.uniform_cube(100, 1)
+    p[17, 1] = np.nan
+    with pytest.raises(P2PError):
+        api.BoxStructure(torch.from_numpy(p).cuda(), (0, 0, 0), 0.25, 4)
+
+
+@pytest.mark.parametrize("occ", [8, 64])
+def test_full_size_sphere_sampled(occ):
+    """Bench workload at full size (2^20 points on the sphere): bit-exact structure, sampled outputs."""
+    api = _cuda()
+    wl = W.sphere_density(occ)
+    lam = W.strengths(wl.n, 1, wl.seed)
+    ref_bins = oracle.bin_points(wl.points, wl.lo, wl.h, wl.ng)
+    targets = np.random.default_rng(occ).choice(wl.n, 3000, replace=False)
+    ref = oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, wl.k)
+    for layout in ("indexed", "redundant"):
+        plan = _plan(api, wl, "helmholtz", layout)
+        assert plan.num_boxes == ref_bins["num_boxes"]
+        np.testing.assert_array_equal(plan.structure.perm.cpu().numpy(), ref_bins["perm"])
+        out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
+        assert rel_l2(out[targets], ref).max() <= TOL
