@@ -67,7 +67,7 @@ def _env_int(name, default):
 # --------------------------------------------------------------- clocks ----
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons every 200 ms."""
+    """Samples nvidia-smi clocks and throttle reasons every 100 ms."""
 
     FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -82,7 +82,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
             return
@@ -141,6 +141,13 @@ def _sample_pairs(struct_host, points, targets) -> int:
     return total
 
 
+def _oracle_call_time(oracle, wl, lam, m, seed):
+    targets = _sample_targets(wl.n, m, seed)
+    t = time.perf_counter()
+    oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, wl.k)
+    return time.perf_counter() - t
+
+
 def cpu_oracle_sample(wls, structs, seconds_per_density: float, seed: int):
     """Times the FP64 oracle (as it stands, single thread) on sampled targets."""
     import oracle
@@ -149,13 +156,11 @@ def cpu_oracle_sample(wls, structs, seconds_per_density: float, seed: int):
     res = []
     for wl, st in zip(wls, structs):
         lam = W.strengths(wl.n, 1, wl.seed)
-        # calibrate with a small call, then size the sample to the time budget
-        probe = _sample_targets(wl.n, 256, seed)
-        t = time.perf_counter()
-        oracle.p2p_targets(wl.points, lam, probe, wl.lo, wl.h, wl.ng, wl.k)
-        t_probe = time.perf_counter() - t
-        per_target = max(t_probe / len(probe), 1e-7)
-        m = int(min(wl.n, max(512, seconds_per_density / per_target)))
+        # calibrate: t(m) = fixed (the oracle's own binning) + m * per_target
+        t_small, t_big = _oracle_call_time(oracle, wl, lam, 256, seed), _oracle_call_time(oracle, wl, lam, 4096, seed)
+        per_target = max((t_big - t_small) / (4096 - 256), 1e-7)
+        fixed = max(t_small - 256 * per_target, 0.0)
+        m = int(min(wl.n, max(512, (seconds_per_density - fixed) / per_target)))
         targets = _sample_targets(wl.n, m, seed + 1)
         t = time.perf_counter()
         ref = oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, wl.k)
@@ -192,15 +197,15 @@ def run_reference(args):
     wls = sweep_workloads()
     structs = [_oracle_structure(wl) for wl in wls]
     lams = [W.strengths(wl.n, 1, wl.seed) for wl in wls]
-    per_density_s = 0.6
-    # size one step: ~per_density_s of oracle work per occupancy
+    per_density_s = 1.0
+    # size one step: ~per_density_s of oracle work per occupancy (t(m) = fixed + m * per_target)
     samples = []
     for i, wl in enumerate(wls):
-        probe = _sample_targets(wl.n, 256, 7)
-        t = time.perf_counter()
-        oracle.p2p_targets(wl.points, lams[i], probe, wl.lo, wl.h, wl.ng, wl.k)
-        per_target = max((time.perf_counter() - t) / len(probe), 1e-7)
-        samples.append(int(min(wl.n, max(256, per_density_s / per_target))))
+        t_small = _oracle_call_time(oracle, wl, lams[i], 256, 7)
+        t_big = _oracle_call_time(oracle, wl, lams[i], 4096, 7)
+        per_target = max((t_big - t_small) / (4096 - 256), 1e-7)
+        fixed = max(t_small - 256 * per_target, 0.0)
+        samples.append(int(min(wl.n, max(256, (per_density_s - fixed) / per_target))))
     times, pairs = [], []
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -220,7 +225,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(args, "oracle"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"per step {samples} sampled targets (occupancy 8/16/32/64), FP64 single thread"},
+                         "sample": f"per step {samples} sampled targets (occupancy 8/16/32/64), FP64 single thread; "
+                                   "each call includes the oracle's own binning of all 2^20 points"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -407,7 +413,8 @@ def run_ours(args):
         cpu_s = sum(r["seconds"] for r in res)
         cpu = {"value": cpu_pairs / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "FP64 oracle on " + ", ".join(f"{len(r['targets'])} targets at occupancy {r['occupancy']}"
-                                                       for r in res) + f" ({cpu_pairs} pairs, {cpu_s:.1f} s)"}
+                                                       for r in res) + f" ({cpu_pairs} pairs, {cpu_s:.1f} s; each call "
+                                                                       "includes the oracle's own binning of all 2^20 points)"}
         errs = []
         for r, out in zip(res, outs):
             got = out.cpu().numpy()[r["targets"]]
@@ -436,7 +443,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--layout", choices=("auto", "indexed", "redundant"), default="indexed")

@@ -96,7 +96,9 @@ __device__ __forceinline__ void stage_sources(const PairArgs& a, int b, int s0, 
     }
 }
 
-// Chooses targets-per-lane TT in {1, 2, 4} minimising lane iterations.
+// Chooses targets-per-lane TT in {1, 2, 4} minimising the lane's instruction
+// count: ceil(ns / Q) iterations of TT pair evaluations (~20 instructions
+// each) plus the per-iteration source loads and loop control (~4).
 __device__ __forceinline__ int choose_tt(int nt, int ns) {
     int best = 4, best_cost = 0x7fffffff;
 #pragma unroll
@@ -104,7 +106,7 @@ __device__ __forceinline__ int choose_tt(int nt, int ns) {
         const int g = (nt + tt - 1) / tt;
         if (g > 32) continue;
         const int q = 32 / g;
-        const int cost = tt * ((ns + q - 1) / q);
+        const int cost = (20 * tt + 4) * ((ns + q - 1) / q);
         if (cost < best_cost) {
             best_cost = cost;
             best = tt;
