@@ -256,6 +256,21 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
 P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, const void* g, float* grad,
                                    int32_t nrhs, int64_t ld, p2p_stream_t stream);
 
+/*
+ * Self-check of the tensor-core operand path (not part of the operator): one
+ * thread block computes D = A . B^T through the same BF16 hi/lo split, shared-
+ * memory layout, descriptors and tcgen05 MMAs as the multi-RHS P2P path.
+ *
+ *   A       [dev] 128 x K float, row-major
+ *   B       [dev] n x K float, row-major
+ *   D       [dev] out, 128 x n float, row-major
+ *   K             multiple of 64, >= 64
+ *   n             multiple of 16, 16 .. 256
+ *   status  [dev] one unsigned int; bit 2 is set if a bounded wait ran out
+ */
+P2P_API p2p_status p2p_diag_tc_gemm(const float* A, const float* B, float* D, int32_t K, int32_t n,
+                                    unsigned int* status, p2p_stream_t stream);
+
 /* Reads and clears the plan's device status word.  Synchronises. */
 P2P_API p2p_status p2p_last_async_status(const p2p_plan* plan, p2p_stream_t stream);
 

@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
             "p2p_apply_staged": ([P, P, i32, i64, i32, ctypes.c_int, P], ctypes.c_int),
             "p2p_grad_points": ([P, P, P, P, i32, i64, P], ctypes.c_int),
             "p2p_last_async_status": ([P, P], ctypes.c_int),
+            "p2p_diag_tc_gemm": ([P, P, P, i32, i32, P, P], ctypes.c_int),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -224,3 +225,8 @@ def p2p_grad_points(plan, lam, g, grad, nrhs, ld, stream=None):
 
 def p2p_last_async_status(plan, stream=None) -> int:
     return load().p2p_last_async_status(plan, _stream(stream))
+
+
+def p2p_diag_tc_gemm(A, B, D, status, stream=None):
+    check(load().p2p_diag_tc_gemm(_ptr(A), _ptr(B), _ptr(D), int(A.shape[1]), int(B.shape[0]), _ptr(status),
+                                  _stream(stream)), "p2p_diag_tc_gemm")

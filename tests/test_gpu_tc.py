@@ -1,0 +1,100 @@
+"""Tensor-core (tcgen05, BF16 hi/lo) multi-RHS path against the FP64 oracle.
+
+Tolerance: relative L2 error per right-hand side <= 1e-5, the bound the FP32
+path meets; the three-product BF16 split (hi.hi + hi.lo + lo.hi) leaves a
+per-product error near 2^-17 that averages down over the neighbourhood sums.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_01596_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_01596_gb300 import api
+    return api
+
+
+def rel_l2(x, ref):
+    x = np.asarray(x).reshape(ref.shape[0], -1)
+    ref = np.asarray(ref).reshape(ref.shape[0], -1)
+    return np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+@pytest.mark.parametrize("n,K", [(16, 64), (64, 128), (256, 192), (48, 320)])
+def test_tc_operand_layout(n, K):
+    _api()
+    from paper_2403_01596_gb300 import _capi as C
+    g = torch.Generator().manual_seed(n + K)
+    A = torch.randn(128, K, generator=g, dtype=torch.float32)
+    B = torch.randn(n, K, generator=g, dtype=torch.float32)
+    D = torch.empty(128, n, dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C.p2p_diag_tc_gemm(A.cuda(), B.cuda(), D, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = (A.double() @ B.double().T).numpy()
+    err = np.linalg.norm(D.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < 2e-5, err
+
+
+def _sphere(n, ng, seed):
+    p = W.unit_sphere(n, seed)
+    h = 2.0 / ng
+    return W.Workload("sphere", p, (-1.0, -1.0, -1.0), h, ng, 2 * np.pi / (5 * h), seed)
+
+
+@pytest.mark.parametrize("nrhs", [16, 24, 64])
+@pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
+def test_tc_apply_parity(nrhs, kernel):
+    api = _api()
+    wl = _sphere(20000, 24, 31)
+    lam = W.strengths(wl.n, nrhs, 31)
+    k = wl.k if kernel == "helmholtz" else 0.0
+    plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, k, kernel=kernel, max_nrhs=nrhs)
+    out = plan.apply(torch.from_numpy(lam).cuda(), path="tc_bf16x3").cpu().numpy()
+    assert plan.async_status() == 0
+    ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, k,
+                     kernel=oracle.HELMHOLTZ if kernel == "helmholtz" else oracle.LAPLACE)
+    err = rel_l2(out, ref)
+    assert err.max() <= TOL, err
+
+
+def test_tc_dense_boxes_and_adjoint():
+    """Boxes with more than 64 targets take several target groups."""
+    api = _api()
+    wl = W.cube_dense(32768, 0)
+    nrhs = 32
+    lam = W.strengths(wl.n, nrhs, 5)
+    plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, wl.k, max_nrhs=nrhs)
+    assert plan.info["n"] == wl.n
+    out = plan.apply(torch.from_numpy(lam).cuda(), path="tc_bf16x3").cpu().numpy()
+    ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
+    assert rel_l2(out, ref).max() <= TOL
+    adj = plan.apply(torch.from_numpy(lam).cuda(), adjoint=True, path="tc_bf16x3").cpu().numpy()
+    ref_adj = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k, adjoint=True)
+    assert rel_l2(adj, ref_adj).max() <= TOL
+
+
+def test_tc_matches_fp32_paths_and_auto_dispatch():
+    api = _api()
+    wl = _sphere(30000, 28, 33)
+    nrhs = 64
+    lam = torch.from_numpy(W.strengths(wl.n, nrhs, 33)).cuda()
+    plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, wl.k, max_nrhs=nrhs)
+    tc = plan.apply(lam, path="tc_bf16x3").cpu().numpy()
+    auto = plan.apply(lam).cpu().numpy()
+    fp = plan.apply(lam, path="fp32_shared").cpu().numpy()
+    np.testing.assert_array_equal(auto, tc)  # nrhs >= 16 dispatches to the tensor-core path
+    assert rel_l2(tc, fp).max() <= 2 * TOL
+    targets = np.random.default_rng(0).choice(wl.n, 500, replace=False)
+    ref = oracle.p2p_targets(wl.points, lam.cpu().numpy(), targets, wl.lo, wl.h, wl.ng, wl.k)
+    assert rel_l2(tc[targets], ref).max() <= TOL
