@@ -172,6 +172,7 @@ struct TcArgs {
     int64_t ld;
     int32_t nrhs;
     int32_t np;            // nrhs rounded up to a multiple of 16 (MMA N)
+    int32_t nacc;          // TMEM accumulators the stages rotate over (1, 2 or 4)
     int32_t tmem_cols;
     int32_t laplace;
     float k;
@@ -345,7 +346,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2p_tc(const TcArgs a) {
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_stage(tmem, smem_u32(A_hi), smem_u32(A_lo), smem_u32(B_hi), smem_u32(B_lo), idesc, st == 0);
+            // stage st accumulates into accumulator st % nacc: shorter accumulation chains
+            const uint32_t acc = tmem + (uint32_t)((st % a.nacc) * np);
+            issue_stage(acc, smem_u32(A_hi), smem_u32(A_lo), smem_u32(B_hi), smem_u32(B_lo), idesc, st < a.nacc);
             mma_commit(&sm.bars[bi]);
         }
         committed = st + 1;
@@ -372,9 +375,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2p_tc(const TcArgs a) {
         const bool odd = (m & 1) != 0;
         const bool write = t < nt;
         const int64_t row = write ? (int64_t)a.perm[tb + t0 + t] * a.ld : 0;
+        const int used = min(a.nacc, nstages);
         for (int c0 = 0; c0 < np; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            for (int q = 1; q < used; ++q) {
+                float w[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * np + c0), w);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] += w[i];
+            }
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const float x = __shfl_xor_sync(P2P_FULL_MASK, odd ? v[i] : v[8 + i], 1);
@@ -501,11 +511,19 @@ p2p_status p2p_apply_tc(const p2p_plan* plan, const float2* lam_sorted, float2* 
     a.ld = ld;
     a.nrhs = nrhs;
     a.np = (nrhs + 15) / 16 * 16;
-    a.tmem_cols = tmem_cols_for(a.np);
+    const int smem_needed = tc_smem_bytes(a.np);
+    int max_smem = 0, dev = 0;
+    P2P_TRY_CUDA(cudaGetDevice(&dev), "p2p_apply_tc");
+    P2P_TRY_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev), "p2p_apply_tc");
+    const int ctas_per_sm = max(1, max_smem / (smem_needed + 1024));
+    // up to four accumulators while the co-resident CTAs' TMEM fits in 512 columns
+    a.nacc = 4;
+    while (a.nacc > 1 && ctas_per_sm * tmem_cols_for(a.nacc * a.np) > 512) a.nacc >>= 1;
+    a.tmem_cols = tmem_cols_for(a.nacc * a.np);
     a.laplace = plan->kernel == P2P_LAPLACE;
     a.k = adjoint ? -plan->k : plan->k;
     a.status = plan->status;
-    const int smem = tc_smem_bytes(a.np);
+    const int smem = smem_needed;
     P2P_TRY_CUDA(cudaFuncSetAttribute(k_p2p_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "p2p_apply_tc");
     const int groups = (plan->max_box + kTcTargets - 1) / kTcTargets;
     dim3 grid((unsigned)plan->nb, (unsigned)groups);
