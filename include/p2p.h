@@ -136,6 +136,34 @@ P2P_API p2p_status p2p_bin_points(const float* pts, int64_t n, const double lo[3
                                   int32_t* perm, int32_t* point_box, int64_t* box_keys, int32_t* box_ptr,
                                   int32_t* num_boxes, void* work, size_t work_bytes, p2p_stream_t stream);
 
+/*
+ * Allocation-free variant of p2p_bin_points.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory when
+ * they bin points: code running while a stream is captured into a CUDA graph
+ * (an allocation there is not part of the graph and can break the capture),
+ * real-time or embedded hosts that fix their device memory budget up front,
+ * and plug-ins whose host application owns every allocation.
+ *
+ * Inputs, outputs and results are those of p2p_bin_points; there is no work
+ * argument.  The scratch lives in one fixed device array inside the library,
+ * sized for at most P2P_BIN_STATIC_MAX_POINTS points (about 2 MiB); every GPU
+ * that loads the library keeps that array until the process exits.  n above
+ * the maximum returns P2P_ERR_INVALID without touching the device.  The call
+ * performs no cudaMalloc, cudaFree or other allocation.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and keeps it; make that first call before any stream
+ * capture.  All calls on a device share the array, which keeps the previous
+ * call's contents (the call clears what it needs zeroed): calls that overlap
+ * on the GPU -- on different streams, or from different host threads on the
+ * same device -- race on it and must be serialised by the caller.
+ * Synchronises, as p2p_bin_points does.
+ */
+#define P2P_BIN_STATIC_MAX_POINTS 65536
+P2P_API p2p_status p2p_bin_points_static(const float* pts, int64_t n, const double lo[3], double h, int32_t ng,
+                                         int32_t* perm, int32_t* point_box, int64_t* box_keys, int32_t* box_ptr,
+                                         int32_t* num_boxes, p2p_stream_t stream);
+
 /* ---------------------------------------------------- neighbour lists --- */
 /*
  * Sec. 3.2 (the per-box list of neighbouring sources and its "second order

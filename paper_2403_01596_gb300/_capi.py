@@ -73,6 +73,7 @@ def load(build_if_missing: bool = True):
             "p2p_version": ([], i32),
             "p2p_bin_workspace_size": ([i64, PSZ], ctypes.c_int),
             "p2p_bin_points": ([P, i64, P, dbl, i32, P, P, P, P, PI32, P, sz, P], ctypes.c_int),
+            "p2p_bin_points_static": ([P, i64, P, dbl, i32, P, P, P, P, PI32, P], ctypes.c_int),
             "p2p_neighbors_workspace_size": ([i32, PSZ], ctypes.c_int),
             "p2p_build_neighbors": ([P, P, i32, i32, P, P, PI64, PI64, P, sz, P], ctypes.c_int),
             "p2p_plan_workspace_size": ([i64, i32, i64, i64, ctypes.c_int, i32, P, PSZ], ctypes.c_int),
@@ -129,6 +130,19 @@ def p2p_bin_points(pts, lo, h, ng, perm, point_box, box_keys, box_ptr, work, str
                                _ptr(box_keys), _ptr(box_ptr), ctypes.byref(nb), _ptr(work), work.numel(),
                                _stream(stream))
     check(st, "p2p_bin_points")
+    return nb.value
+
+
+P2P_BIN_STATIC_MAX_POINTS = 65536
+
+
+def p2p_bin_points_static(pts, lo, h, ng, perm, point_box, box_keys, box_ptr, stream=None) -> int:
+    """p2p_bin_points without a workspace (scratch in a fixed device array, n <= 65536)."""
+    nb = ctypes.c_int32(0)
+    st = load().p2p_bin_points_static(_ptr(pts), pts.shape[0], _lo(lo), float(h), int(ng), _ptr(perm),
+                                      _ptr(point_box), _ptr(box_keys), _ptr(box_ptr), ctypes.byref(nb),
+                                      _stream(stream))
+    check(st, "p2p_bin_points_static")
     return nb.value
 
 
