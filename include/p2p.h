@@ -284,6 +284,46 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
 P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, const void* g, float* grad,
                                    int32_t nrhs, int64_t ld, p2p_stream_t stream);
 
+/* ----------------------------------------------------- batched apply --- */
+/*
+ * Several independent geometries (plans) applied in one persistent launch.
+ * The paper splits large problems into pieces of 50k - 150k points to keep its
+ * repetition kernel near its optimum (Sec. 4.3); a batch runs such pieces, or
+ * unrelated geometries of uneven box occupancy, together: work items of every
+ * plan form one queue ordered by decreasing cost (targets x sources) that the
+ * warps of a persistent grid drain with an atomic counter.
+ *
+ *   plans           [host] count plan pointers, 1 <= count <= 16; the plans must
+ *                          outlive the batch and are applied with nrhs columns
+ *   nrhs                   1 .. min over plans of max_nrhs
+ *   warps_per_cta          0 (default 8) or 1 .. 16
+ *   workspace       [dev]  at least p2p_batch_workspace_size bytes, 256-byte aligned
+ *
+ * p2p_batch_create synchronises once (it sorts the work queue on the device).
+ * p2p_batch_apply takes host arrays of count device pointers: lambdas[g] and
+ * outs[g] are plan g's n_g x nrhs complex64 strengths and results, leading
+ * dimension ld (same for all).  It enqueues two kernels and no allocation or
+ * synchronisation, so it may be captured in a CUDA graph;
+ * p2p_batch_graph_create does exactly that for fixed buffers (the graph reads
+ * lambdas and writes outs every time p2p_batch_graph_launch replays it; update
+ * the buffers' contents in place between replays).  A batch shares its plans'
+ * staging buffers: do not apply those plans concurrently with the batch.
+ */
+typedef struct p2p_batch p2p_batch;
+P2P_API p2p_status p2p_batch_workspace_size(const p2p_plan* const* plans, int32_t count, int32_t nrhs,
+                                            size_t* bytes);
+P2P_API p2p_status p2p_batch_create(p2p_batch** batch, const p2p_plan* const* plans, int32_t count, int32_t nrhs,
+                                    int32_t warps_per_cta, void* workspace, size_t workspace_bytes,
+                                    p2p_stream_t stream);
+P2P_API p2p_status p2p_batch_apply(const p2p_batch* batch, const void* const* lambdas, void* const* outs, int64_t ld,
+                                   p2p_stream_t stream);
+P2P_API p2p_status p2p_batch_graph_create(p2p_batch* batch, const void* const* lambdas, void* const* outs,
+                                          int64_t ld);
+P2P_API p2p_status p2p_batch_graph_launch(const p2p_batch* batch, p2p_stream_t stream);
+P2P_API p2p_status p2p_batch_info(const p2p_batch* batch, int64_t* work_items, int32_t* grid,
+                                  int32_t* warps_per_cta);
+P2P_API p2p_status p2p_batch_destroy(p2p_batch* batch);
+
 /*
  * Self-check of the tensor-core operand path (not part of the operator): one
  * thread block computes D = A . B^T through the same BF16 hi/lo split, shared-

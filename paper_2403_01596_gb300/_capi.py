@@ -90,6 +90,13 @@ def load(build_if_missing: bool = True):
             "p2p_grad_points": ([P, P, P, P, i32, i64, P], ctypes.c_int),
             "p2p_last_async_status": ([P, P], ctypes.c_int),
             "p2p_diag_tc_gemm": ([P, P, P, i32, i32, P, P], ctypes.c_int),
+            "p2p_batch_workspace_size": ([P, i32, i32, PSZ], ctypes.c_int),
+            "p2p_batch_create": ([ctypes.POINTER(P), P, i32, i32, i32, P, sz, P], ctypes.c_int),
+            "p2p_batch_apply": ([P, P, P, i64, P], ctypes.c_int),
+            "p2p_batch_graph_create": ([P, P, P, i64], ctypes.c_int),
+            "p2p_batch_graph_launch": ([P, P], ctypes.c_int),
+            "p2p_batch_info": ([P, PI64, PI32, PI32], ctypes.c_int),
+            "p2p_batch_destroy": ([P], ctypes.c_int),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -244,3 +251,48 @@ def p2p_last_async_status(plan, stream=None) -> int:
 def p2p_diag_tc_gemm(A, B, D, status, stream=None):
     check(load().p2p_diag_tc_gemm(_ptr(A), _ptr(B), _ptr(D), int(A.shape[1]), int(B.shape[0]), _ptr(status),
                                   _stream(stream)), "p2p_diag_tc_gemm")
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = t if isinstance(t, int) else (t.value if isinstance(t, ctypes.c_void_p) else t.data_ptr())
+    return arr
+
+
+def p2p_batch_workspace_size(plans, nrhs) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().p2p_batch_workspace_size(_ptr_array(plans), len(plans), int(nrhs), ctypes.byref(out)),
+          "p2p_batch_workspace_size")
+    return out.value
+
+
+def p2p_batch_create(plans, nrhs, warps_per_cta, workspace, stream=None):
+    batch = ctypes.c_void_p(0)
+    check(load().p2p_batch_create(ctypes.byref(batch), _ptr_array(plans), len(plans), int(nrhs), int(warps_per_cta),
+                                  _ptr(workspace), workspace.numel(), _stream(stream)), "p2p_batch_create")
+    return batch
+
+
+def p2p_batch_apply(batch, lams, outs, ld, stream=None):
+    check(load().p2p_batch_apply(batch, _ptr_array(lams), _ptr_array(outs), int(ld), _stream(stream)),
+          "p2p_batch_apply")
+
+
+def p2p_batch_graph_create(batch, lams, outs, ld):
+    check(load().p2p_batch_graph_create(batch, _ptr_array(lams), _ptr_array(outs), int(ld)), "p2p_batch_graph_create")
+
+
+def p2p_batch_graph_launch(batch, stream=None):
+    check(load().p2p_batch_graph_launch(batch, _stream(stream)), "p2p_batch_graph_launch")
+
+
+def p2p_batch_info(batch) -> dict:
+    items, grid, warps = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    check(load().p2p_batch_info(batch, ctypes.byref(items), ctypes.byref(grid), ctypes.byref(warps)), "p2p_batch_info")
+    return {"work_items": items.value, "grid": grid.value, "warps_per_cta": warps.value}
+
+
+def p2p_batch_destroy(batch):
+    if batch:
+        load().p2p_batch_destroy(batch)

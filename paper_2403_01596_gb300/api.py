@@ -147,6 +147,75 @@ class Plan:
             pass
 
 
+class Batch:
+    """Several plans applied in one persistent launch (optionally replayed from a CUDA graph)."""
+
+    def __init__(self, plans, nrhs: int = 1, warps_per_cta: int = 0):
+        self.plans = list(plans)
+        self.nrhs = int(nrhs)
+        handles = [p._plan for p in self.plans]
+        dev = self.plans[0].structure.points.device
+        self.workspace = _bytes(C.p2p_batch_workspace_size(handles, self.nrhs), dev)
+        self._b = C.p2p_batch_create(handles, self.nrhs, warps_per_cta, self.workspace, _stream())
+        self.info = C.p2p_batch_info(self._b)
+        self._graph_buffers = None
+
+    def _views(self, lams, outs):
+        if len(lams) != len(self.plans):
+            raise ValueError("one strength tensor per plan is required")
+        lam2 = [p._check_lam(l).contiguous() for p, l in zip(self.plans, lams)]
+        for l in lam2:
+            if l.shape[1] != self.nrhs:
+                raise ValueError(f"expected {self.nrhs} right-hand sides")
+        if outs is None:
+            outs = [torch.empty_like(l) for l in lam2]
+        outs2 = [o.reshape(l.shape) for o, l in zip(outs, lam2)]
+        return lam2, outs2
+
+    def apply(self, lams, outs=None):
+        lam2, outs2 = self._views(lams, outs)
+        C.p2p_batch_apply(self._b, lam2, outs2, self.nrhs, _stream())
+        return outs2
+
+    def capture(self, lams, outs=None):
+        """Captures one batched apply on these buffers into a CUDA graph; returns the outputs."""
+        lam2, outs2 = self._views(lams, outs)
+        C.p2p_batch_graph_create(self._b, lam2, outs2, self.nrhs)
+        self._graph_buffers = (lam2, outs2)
+        return outs2
+
+    def replay(self):
+        if self._graph_buffers is None:
+            raise RuntimeError("capture() first")
+        C.p2p_batch_graph_launch(self._b, _stream())
+        return self._graph_buffers[1]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            C.p2p_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def choose_grid_ct(points: torch.Tensor, lo, extent: float, ct: int, ng_start: int = 1,
+                   ng_max: int = 1 << 21) -> BoxStructure:
+    """Leaf grid by clustering threshold (Sec. 3.1): raise the tree level, doubling
+    the boxes per axis, until no leaf box holds more than `ct` points."""
+    ng = max(1, int(ng_start))
+    while True:
+        st = BoxStructure(points, lo, float(extent) / ng, ng)
+        occ = int((st.box_ptr[1:] - st.box_ptr[:-1]).max().item()) if st.num_boxes else 0
+        if occ <= ct or ng * 2 > ng_max:
+            st.max_occupancy = occ
+            return st
+        ng *= 2
+
+
 class P2PFunction(torch.autograd.Function):
     """out = A(x) lam with gradients for lam (A^H g) and for x (radial-derivative kernel).
 

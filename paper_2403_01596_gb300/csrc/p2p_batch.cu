@@ -1,0 +1,390 @@
+// Persistent batched P2P over several independent geometries (plans).
+//
+// One batched apply is two kernel launches, both safe to capture in a CUDA
+// graph (no allocation, no host synchronisation, every pointer passed by
+// value):
+//   k_batch_stage   writes each geometry's output pointer into the device
+//                   geometry table, gathers every geometry's strengths into its
+//                   plan's staging buffer (sorted or packed rows), zeroes the
+//                   outputs that are accumulated with atomics and resets the
+//                   work-queue counter;
+//   k_pair_batched  a persistent grid (resident blocks x SMs) whose warps take
+//                   work items (geometry, box, source chunk) from one global
+//                   queue with an atomic counter; the queue is ordered by
+//                   decreasing item cost (targets x sources), so the heaviest
+//                   boxes of the most crowded geometry start first and the
+//                   small ones fill the tail.  A warp leaves when the counter
+//                   passes the end; there is no waiting on other warps.
+// The per-item work is the same device code as the per-plan pair kernel.
+#include <string.h>
+
+#include <algorithm>
+
+#include "p2p_pair.cuh"
+
+using namespace p2p_detail;
+using namespace p2p_pair;
+
+namespace {
+
+constexpr int kMaxBatch = 16;
+
+struct BatchGeom {
+    PairArgs a;
+    int32_t kernel;
+    int32_t red;
+    int64_t n;
+    int64_t nrows;         // staged rows (points or packed entries)
+    const int32_t* rows;   // original index of every staged row (-1: padding)
+};
+
+struct BatchIO {
+    const float2* lam[kMaxBatch];
+    float2* out[kMaxBatch];
+    int64_t row_off[kMaxBatch + 1];  // prefix over geometries of staged rows * nrhs
+    int64_t out_off[kMaxBatch + 1];  // prefix over atomic geometries of n * nrhs (0 for the others)
+    int32_t count;
+    int32_t nrhs;
+    int64_t ld;
+};
+
+struct ItemOffsets {
+    int64_t off[kMaxBatch + 1];
+    int32_t count;
+};
+
+__device__ __forceinline__ int find_geom(const int64_t* off, int count, int64_t i) {
+    int g = 0;
+    while (g + 1 < count && off[g + 1] <= i) ++g;
+    return g;
+}
+
+__global__ void k_batch_stage(BatchGeom* __restrict__ geoms, const BatchIO io, unsigned long long* __restrict__ counter) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (tid < io.count) {
+        geoms[tid].a.out = io.out[tid];
+        geoms[tid].a.ld = io.ld;
+        geoms[tid].a.nrhs = io.nrhs;
+    }
+    if (tid == 0) *counter = 0ull;
+    const int64_t rows_total = io.row_off[io.count];
+    for (int64_t i = tid; i < rows_total; i += stride) {
+        const int g = find_geom(io.row_off, io.count, i);
+        const int64_t li = i - io.row_off[g];
+        const int64_t s = li / io.nrhs;
+        const int q = (int)(li - s * io.nrhs);
+        const int32_t r = geoms[g].rows[s];
+        float2* dst = const_cast<float2*>(geoms[g].a.lam);
+        dst[li] = r >= 0 ? io.lam[g][(int64_t)r * io.ld + q] : make_float2(0.f, 0.f);
+    }
+    const int64_t outs_total = io.out_off[io.count];
+    for (int64_t i = tid; i < outs_total; i += stride) {
+        const int g = find_geom(io.out_off, io.count, i);
+        const int64_t li = i - io.out_off[g];
+        const int64_t row = li / io.nrhs;
+        const int q = (int)(li - row * io.nrhs);
+        io.out[g][row * io.ld + q] = make_float2(0.f, 0.f);
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(512) k_pair_batched(const BatchGeom* __restrict__ geoms, const int2* __restrict__ order,
+                                                      int64_t total, unsigned long long* __restrict__ counter,
+                                                      int warp_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* ws = smem_raw + (size_t)warp * warp_bytes;
+    for (;;) {
+        unsigned long long idx = 0;
+        if (lane == 0) idx = atomicAdd(counter, 1ull);
+        idx = __shfl_sync(P2P_FULL_MASK, idx, 0);
+        if (idx >= (unsigned long long)total) break;
+        const int2 o = order[idx];
+        const BatchGeom& G = geoms[o.x];
+        if (G.kernel == P2P_HELMHOLTZ) {
+            if (G.red) process_item<P2P_HELMHOLTZ, R, true>(G.a, o.y, ws, lane);
+            else process_item<P2P_HELMHOLTZ, R, false>(G.a, o.y, ws, lane);
+        } else {
+            if (G.red) process_item<P2P_LAPLACE, R, true>(G.a, o.y, ws, lane);
+            else process_item<P2P_LAPLACE, R, false>(G.a, o.y, ws, lane);
+        }
+    }
+}
+
+// Sort key of every item: larger cost (targets x staged sources) first.
+__global__ void k_batch_keys(const BatchGeom* __restrict__ geoms, const ItemOffsets off, uint64_t* __restrict__ keys,
+                             int32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= off.off[off.count]) return;
+    const int g = find_geom(off.off, off.count, i);
+    const PairArgs& a = geoms[g].a;
+    const int4 it = a.items[i - off.off[g]];
+    const int b = it.x;
+    const int64_t nt = a.box_ptr[b + 1] - a.box_ptr[b];
+    const int64_t ns = min(a.chunk, a.box_src[b] - it.y);
+    const uint64_t cost = (uint64_t)min(nt * ns, (int64_t)0xFFFFFFFF);
+    keys[i] = 0xFFFFFFFFull - cost;
+    vals[i] = (int32_t)i;
+}
+
+__global__ void k_batch_order(const int32_t* __restrict__ sorted, const ItemOffsets off, int2* __restrict__ order) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= off.off[off.count]) return;
+    const int64_t v = sorted[i];
+    const int g = find_geom(off.off, off.count, v);
+    order[i] = make_int2(g, (int)(v - off.off[g]));
+}
+
+struct BatchLayout {
+    BatchGeom* geoms;
+    int2* order;
+    unsigned long long* counter;
+    uint64_t *keys, *keys_alt;
+    int32_t *vals, *vals_alt;
+    void* radix_ws;
+    size_t bytes;
+};
+
+BatchLayout batch_layout(int64_t total, void* ws) {
+    Carver c{static_cast<char*>(ws), 0, (size_t)-1};
+    BatchLayout L;
+    size_t m = (size_t)(total > 0 ? total : 1);
+    L.geoms = c.take<BatchGeom>(kMaxBatch);
+    L.order = c.take<int2>(m);
+    L.counter = c.take<unsigned long long>(1);
+    L.keys = c.take<uint64_t>(m);
+    L.keys_alt = c.take<uint64_t>(m);
+    L.vals = c.take<int32_t>(m);
+    L.vals_alt = c.take<int32_t>(m);
+    L.radix_ws = c.take<char>(radix_workspace_bytes(total));
+    L.bytes = align_up(c.off, 256);
+    return L;
+}
+
+template <int R>
+cudaError_t configure(int warps, int warp_bytes, int* ctas_per_sm) {
+    const int smem = warps * warp_bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_pair_batched<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_pair_batched<R>, warps * 32, smem);
+}
+
+}  // namespace
+
+struct p2p_batch {
+    int32_t count;
+    int32_t nrhs;
+    int32_t R;
+    int32_t warps;
+    int32_t warp_bytes;
+    int32_t grid;
+    int64_t total;
+    const p2p_plan* plans[kMaxBatch];
+    BatchLayout L;
+    BatchIO io;  // row/output prefixes (pointers filled per apply)
+    cudaStream_t capture_stream;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+static p2p_status check_plans(const p2p_plan* const* plans, int32_t count, int32_t nrhs, int64_t* total) {
+    if (!plans || count < 1 || count > kMaxBatch || nrhs < 1 || nrhs > 256) return P2P_ERR_INVALID;
+    int64_t t = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || plans[i]->n == 0 || nrhs > plans[i]->max_nrhs) return P2P_ERR_INVALID;
+        t += plans[i]->n_items;
+    }
+    if (t >= INT32_MAX) return P2P_ERR_UNSUPPORTED;
+    *total = t;
+    return P2P_OK;
+}
+
+static p2p_status batch_launch(const p2p_batch* b, const void* const* lambdas, void* const* outs, int64_t ld,
+                               cudaStream_t s) {
+    BatchIO io = b->io;
+    for (int g = 0; g < b->count; ++g) {
+        if (!lambdas[g] || !outs[g] || ((uintptr_t)lambdas[g] & 7) || ((uintptr_t)outs[g] & 7))
+            return P2P_ERR_INVALID;
+        io.lam[g] = static_cast<const float2*>(lambdas[g]);
+        io.out[g] = static_cast<float2*>(outs[g]);
+    }
+    io.ld = ld;
+    const int64_t work = io.row_off[b->count] > io.out_off[b->count] ? io.row_off[b->count] : io.out_off[b->count];
+    const int threads = 256;
+    int64_t blocks = (work + threads - 1) / threads;
+    if (blocks > 65536) blocks = 65536;
+    if (blocks < 1) blocks = 1;
+    k_batch_stage<<<(unsigned)blocks, threads, 0, s>>>(b->L.geoms, io, b->L.counter);
+    P2P_CHECK_LAUNCH("p2p_batch_apply/stage");
+    const int smem = b->warps * b->warp_bytes;
+    if (b->R == 1) k_pair_batched<1><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total,
+                                                                         b->L.counter, b->warp_bytes);
+    else if (b->R == 2) k_pair_batched<2><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total,
+                                                                              b->L.counter, b->warp_bytes);
+    else k_pair_batched<4><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->L.counter,
+                                                               b->warp_bytes);
+    P2P_CHECK_LAUNCH("p2p_batch_apply/pair");
+    return P2P_OK;
+}
+
+extern "C" {
+
+P2P_API p2p_status p2p_batch_workspace_size(const p2p_plan* const* plans, int32_t count, int32_t nrhs,
+                                            size_t* bytes) {
+    int64_t total = 0;
+    if (!bytes) return P2P_ERR_INVALID;
+    p2p_status st = check_plans(plans, count, nrhs, &total);
+    if (st != P2P_OK) return st;
+    *bytes = batch_layout(total, nullptr).bytes;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_batch_create(p2p_batch** batch, const p2p_plan* const* plans, int32_t count, int32_t nrhs,
+                                    int32_t warps_per_cta, void* workspace, size_t workspace_bytes,
+                                    p2p_stream_t stream) {
+    if (!batch) return P2P_ERR_INVALID;
+    *batch = nullptr;
+    int64_t total = 0;
+    p2p_status st = check_plans(plans, count, nrhs, &total);
+    if (st != P2P_OK) return st;
+    if (warps_per_cta == 0) warps_per_cta = 8;
+    if (warps_per_cta < 1 || warps_per_cta > 16) return P2P_ERR_INVALID;
+    if (!workspace || ((uintptr_t)workspace & 255)) return P2P_ERR_INVALID;
+    BatchLayout L = batch_layout(total, workspace);
+    if (workspace_bytes < L.bytes) return P2P_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    p2p_batch* b = (p2p_batch*)calloc(1, sizeof(p2p_batch));
+    if (!b) return P2P_ERR_ALLOC;
+    b->count = count;
+    b->nrhs = nrhs;
+    b->R = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
+    b->warps = warps_per_cta;
+    b->total = total;
+    b->L = L;
+    int max_chunk = 32;
+    BatchGeom host[kMaxBatch];
+    ItemOffsets off;
+    memset(&off, 0, sizeof(off));
+    memset(&b->io, 0, sizeof(b->io));
+    off.count = count;
+    b->io.count = count;
+    b->io.nrhs = nrhs;
+    for (int g = 0; g < count; ++g) {
+        const p2p_plan* p = plans[g];
+        b->plans[g] = p;
+        host[g].a = base_args(p);
+        host[g].a.nrhs = nrhs;
+        host[g].kernel = p->kernel;
+        host[g].red = p->layout == P2P_LAYOUT_REDUNDANT;
+        host[g].n = p->n;
+        host[g].nrows = host[g].red ? p->packed : p->n;
+        host[g].rows = host[g].red ? p->pk_src : p->perm;
+        max_chunk = std::max(max_chunk, p->tune.chunk);
+        off.off[g + 1] = off.off[g] + p->n_items;
+        b->io.row_off[g + 1] = b->io.row_off[g] + host[g].nrows * nrhs;
+        b->io.out_off[g + 1] = b->io.out_off[g] + (host[g].a.atomic_out ? p->n * nrhs : 0);
+    }
+    b->warp_bytes = warp_smem_bytes(max_chunk, b->R);
+#define FAIL(expr, where)                 \
+    do {                                  \
+        cudaError_t e_ = (expr);          \
+        if (e_ != cudaSuccess) {          \
+            set_cuda_error(e_, where);    \
+            free(b);                      \
+            return P2P_ERR_CUDA;          \
+        }                                 \
+    } while (0)
+    int ctas_per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = b->R == 1 ? configure<1>(b->warps, b->warp_bytes, &ctas_per_sm)
+                  : b->R == 2 ? configure<2>(b->warps, b->warp_bytes, &ctas_per_sm)
+                              : configure<4>(b->warps, b->warp_bytes, &ctas_per_sm);
+    FAIL(e, "p2p_batch_create/occupancy");
+    FAIL(cudaGetDevice(&dev), "p2p_batch_create");
+    FAIL(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "p2p_batch_create");
+    if (ctas_per_sm < 1) {
+        free(b);
+        return P2P_ERR_UNSUPPORTED;
+    }
+    b->grid = ctas_per_sm * sms;
+    FAIL(cudaMemcpyAsync(L.geoms, host, sizeof(BatchGeom) * count, cudaMemcpyHostToDevice, s), "p2p_batch_create");
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    k_batch_keys<<<blocks, 256, 0, s>>>(L.geoms, off, L.keys, L.vals);
+    FAIL(cudaGetLastError(), "p2p_batch_create/keys");
+    bool in_alt = false;
+    FAIL(radix_sort_pairs(L.keys, L.vals, L.keys_alt, L.vals_alt, total, 32, L.radix_ws, s, &in_alt),
+         "p2p_batch_create/sort");
+    k_batch_order<<<blocks, 256, 0, s>>>(in_alt ? L.vals_alt : L.vals, off, L.order);
+    FAIL(cudaGetLastError(), "p2p_batch_create/order");
+    FAIL(cudaStreamSynchronize(s), "p2p_batch_create");
+#undef FAIL
+    *batch = b;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_batch_apply(const p2p_batch* batch, const void* const* lambdas, void* const* outs, int64_t ld,
+                                   p2p_stream_t stream) {
+    if (!batch || !lambdas || !outs || ld < batch->nrhs) return P2P_ERR_INVALID;
+    return batch_launch(batch, lambdas, outs, ld, (cudaStream_t)stream);
+}
+
+P2P_API p2p_status p2p_batch_graph_create(p2p_batch* batch, const void* const* lambdas, void* const* outs,
+                                          int64_t ld) {
+    if (!batch || !lambdas || !outs || ld < batch->nrhs) return P2P_ERR_INVALID;
+    if (batch->exec) return P2P_ERR_INVALID;
+    cudaStream_t cs = nullptr;
+    P2P_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "p2p_batch_graph_create");
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        set_cuda_error(e, "p2p_batch_graph_create/begin");
+        return P2P_ERR_CUDA;
+    }
+    p2p_status st = batch_launch(batch, lambdas, outs, ld, cs);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (st != P2P_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (st != P2P_OK) return st;
+        set_cuda_error(e, "p2p_batch_graph_create/end");
+        return P2P_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        set_cuda_error(e, "p2p_batch_graph_create/instantiate");
+        return P2P_ERR_CUDA;
+    }
+    batch->capture_stream = cs;
+    batch->graph = graph;
+    batch->exec = exec;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_batch_graph_launch(const p2p_batch* batch, p2p_stream_t stream) {
+    if (!batch || !batch->exec) return P2P_ERR_INVALID;
+    P2P_TRY_CUDA(cudaGraphLaunch(batch->exec, (cudaStream_t)stream), "p2p_batch_graph_launch");
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_batch_info(const p2p_batch* batch, int64_t* work_items, int32_t* grid, int32_t* warps_per_cta) {
+    if (!batch) return P2P_ERR_INVALID;
+    if (work_items) *work_items = batch->total;
+    if (grid) *grid = batch->grid;
+    if (warps_per_cta) *warps_per_cta = batch->warps;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_batch_destroy(p2p_batch* batch) {
+    if (!batch) return P2P_OK;
+    if (batch->exec) cudaGraphExecDestroy(batch->exec);
+    if (batch->graph) cudaGraphDestroy(batch->graph);
+    if (batch->capture_stream) cudaStreamDestroy(batch->capture_stream);
+    free(batch);
+    return P2P_OK;
+}
+
+}  // extern "C"

@@ -203,7 +203,9 @@ __global__ void k_items(const int32_t* __restrict__ n_chunks, const int32_t* __r
     for (int32_t i = 0; i < c; ++i) items[o + i] = make_int4(b, i * chunk, 0, 0);
 }
 
-// One warp per box: copy the neighbourhood's sources into the box's packed tile.
+// One warp per box: copy the neighbourhood's sources into the box's packed
+// tile, the box's own sources first, then the other neighbour boxes in
+// ascending id (the order the pair kernel's r = 0 mask relies on).
 __global__ void k_pack(const float4* __restrict__ xs, const int32_t* __restrict__ perm,
                        const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ nbr_ptr,
                        const int32_t* __restrict__ nbr_idx, const int32_t* __restrict__ pk_off, int32_t nb,
@@ -212,11 +214,15 @@ __global__ void k_pack(const float4* __restrict__ xs, const int32_t* __restrict_
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
     const int32_t e0 = nbr_ptr[b], ne = nbr_ptr[b + 1] - e0;
+    const int32_t c = lane < ne ? nbr_idx[e0 + lane] : -1;
+    const unsigned selfm = __ballot_sync(P2P_FULL_MASK, c == (int32_t)b);
+    const int sp = selfm ? __ffs(selfm) - 1 : 0;
+    const int from = lane == 0 ? sp : (lane <= sp ? lane - 1 : lane);
+    const int32_t cs = __shfl_sync(P2P_FULL_MASK, c, from);
     int32_t start = 0, len = 0;
     if (lane < ne) {
-        int32_t c = nbr_idx[e0 + lane];
-        start = box_ptr[c];
-        len = box_ptr[c + 1] - start;
+        start = box_ptr[cs];
+        len = box_ptr[cs + 1] - start;
     }
     int32_t incl = len;
 #pragma unroll
