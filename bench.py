@@ -440,6 +440,187 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------- extension workloads --
+# Non-default modes (python bench.py --workload multirhs|grad|batched): the
+# 64-RHS tensor-core comparison on the 2:1:1 ellipsoid, the differentiable
+# step on the sphere, and the batched uneven geometries.  Each prints one JSON
+# line of the same shape as the default occupancy sweep.
+
+def _events_time(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms), ms
+
+
+def _oracle_sampled(wl, lam_np, targets, adjoint=False):
+    import oracle
+    oracle.build()
+    t = time.perf_counter()
+    ref = oracle.p2p_targets(wl.points, lam_np, targets, wl.lo, wl.h, wl.ng, wl.k, adjoint=adjoint)
+    return ref, time.perf_counter() - t
+
+
+def _rel_l2_cols(x, ref):
+    x = np.asarray(x).reshape(ref.shape[0], -1)
+    ref = np.asarray(ref).reshape(ref.shape[0], -1)
+    return np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+def run_multirhs(args):
+    import torch
+    from paper_2403_01596_gb300 import api, workloads as W
+    torch.cuda.set_device(0)
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(0)
+    wl = W.ellipsoid_multirhs(int((1 << 21) * args.scale))
+    nrhs = 64
+    pts = torch.from_numpy(wl.points).cuda()
+    plan = api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k, max_nrhs=nrhs)
+    lam_np = W.strengths(wl.n, nrhs, wl.seed)
+    lam = torch.from_numpy(lam_np).cuda()
+    out = torch.empty_like(lam)
+    P = plan.pair_count()
+    stream = torch.cuda.current_stream()
+    res = {}
+    for path, steps in (("tc_bf16x3", args.ext_steps), ("fp32_shared", max(2, args.ext_steps // 4)),
+                        ("fp32_per_rhs", max(2, args.ext_steps // 8))):
+        med, _ = _events_time(lambda: plan.apply(lam, out=out, path=path), steps, 2, stream)
+        res[path] = {"ms": med, "gpair_rhs_s": P * nrhs / med / 1e6, "out": out.cpu().numpy()}
+    targets = _sample_targets(wl.n, args.samples, 5)
+    ref, cpu_s = _oracle_sampled(wl, lam_np, targets)
+    for path in res:
+        e = _rel_l2_cols(res[path].pop("out")[targets], ref)
+        res[path]["rel_l2_max"] = float(e.max())
+        res[path]["rel_l2_per_rhs_mean"] = float(e.mean())
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    mufu_peak = props.multi_processor_count * 16 * f_max / 3 / 1e9        # G evaluations per second (G/s)
+    tc_flops = 3 * 8 * P * nrhs                                           # hi.hi + hi.lo + lo.hi, realified complex
+    t_tc = res["tc_bf16x3"]["ms"] * 1e-3
+    line = {"metric": METRIC + " [64-RHS: pair x RHS]", "value": res["tc_bf16x3"]["gpair_rhs_s"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.ext_steps, "warmup": 2, "ms_per_step": res["tc_bf16x3"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/f32",
+            "data": "synthetic",
+            "config": {"workload": "ellipsoid211_multirhs", "n_points": wl.n, "grid": wl.ng, "nrhs": nrhs,
+                       "pairs": P, "boxes": plan.num_boxes},
+            "paths": res,
+            "speedup_tc_vs_fp32_per_rhs": res["fp32_per_rhs"]["ms"] / res["tc_bf16x3"]["ms"],
+            "speedup_tc_vs_fp32_shared": res["fp32_shared"]["ms"] / res["tc_bf16x3"]["ms"],
+            "roofline": {"bound": "alu", "achieved": P / t_tc / 1e9, "peak": mufu_peak, "unit": "G pair-evaluations/s",
+                         "frac": P / t_tc / 1e9 / mufu_peak,
+                         "tensor_tflops": tc_flops / t_tc / 1e12,
+                         "tensor_frac_of_bf16_peak": tc_flops / t_tc / 1e12 / float(peaks["bf16_tflops"])},
+            "cpu_baseline": {"value": len(targets) * nrhs * (P / wl.n) / cpu_s / 1e9, "unit": UNIT, "cores": 1,
+                             "kind": "oracle", "sample": f"{len(targets)} targets x {nrhs} RHS (pairs estimated "
+                                                         f"from the mean neighbourhood), {cpu_s:.1f} s"}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_grad(args):
+    import torch
+    from paper_2403_01596_gb300 import api, workloads as W
+    torch.cuda.set_device(0)
+    wl = W.sphere_grad(int((1 << 18) * args.scale))
+    pts = torch.from_numpy(wl.points).cuda().requires_grad_(True)
+    plan = api.Plan(pts.detach(), wl.lo, wl.h, wl.ng, wl.k)
+    lam = torch.from_numpy(W.strengths(wl.n, 1, wl.seed)).cuda().requires_grad_(True)
+    b = torch.from_numpy(W.strengths(wl.n, 1, 4)).cuda()
+    P = plan.pair_count()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lam.grad = None
+        pts.grad = None
+        out = api.p2p(lam, pts, plan)
+        loss = (out - b).abs().pow(2).sum()
+        loss.backward()
+
+    med, _ = _events_time(step, args.ext_steps, 3, stream)
+    import oracle
+    oracle.build()
+    g = 2 * (plan.apply(lam.detach()) - b)
+    t = time.perf_counter()
+    ref_x = oracle.grad_points(wl.points, lam.detach().cpu().numpy(), g.cpu().numpy(), wl.lo, wl.h, wl.ng, wl.k)
+    cpu_s = time.perf_counter() - t
+    step()
+    torch.cuda.synchronize()
+    err_x = float(np.linalg.norm(pts.grad.cpu().numpy() - ref_x) / np.linalg.norm(ref_x))
+    line = {"metric": METRIC + " [forward + adjoint + coordinate gradient: 3 sweeps per step]",
+            "value": 3 * P / med / 1e6, "unit": UNIT, "n_gpus": 1, "steps": args.ext_steps, "warmup": 3,
+            "ms_per_step": med, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sphere_grad", "n_points": wl.n, "grid": wl.ng, "k": wl.k, "pairs": P,
+                       "loss": "||A(x) lam - b||^2"},
+            "grad_x_rel_l2_vs_fp64": err_x,
+            "cpu_baseline": {"value": P / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"full FP64 coordinate gradient ({P} pairs, {cpu_s:.1f} s)"}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_batched(args):
+    import torch
+    from paper_2403_01596_gb300 import api, workloads as W
+    torch.cuda.set_device(0)
+    nrhs = 8
+    plans, lams, geos, pairs = [], [], [], []
+    t_plan = time.perf_counter()
+    for g in range(len(W.BATCH_SIZES)):
+        geo = W.batch_geometry(g, args.scale)
+        pts = torch.from_numpy(geo["points"]).cuda()
+        st = api.choose_grid_ct(pts, geo["lo"], geo["extent"], 128, ng_start=16)
+        k = 2 * np.pi * geo["edge_wavelengths"] / st.h
+        plan = api.Plan(pts, geo["lo"], st.h, st.ng, k, max_nrhs=nrhs, structure=st)
+        plans.append(plan)
+        geos.append(W.Workload(f"batch{g}", geo["points"], geo["lo"], st.h, st.ng, k, geo["seed"],
+                               {"max_occupancy": st.max_occupancy}))
+        lams.append(torch.from_numpy(W.strengths(plan.n, nrhs, geo["seed"])).cuda())
+        pairs.append(plan.pair_count())
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t_plan
+    batch = api.Batch(plans, nrhs=nrhs)
+    outs = batch.capture(lams)
+    stream = torch.cuda.current_stream()
+    med, _ = _events_time(batch.replay, args.ext_steps, 3, stream)
+    # the same work as separate per-plan applies, for comparison
+    sep, _ = _events_time(lambda: [p.apply(l) for p, l in zip(plans, lams)], max(2, args.ext_steps // 2), 2, stream)
+    batch.replay()
+    torch.cuda.synchronize()
+    errs, cpu_pairs, cpu_s = [], 0, 0.0
+    for geo, plan, lam, out in zip(geos, plans, lams, outs):
+        targets = _sample_targets(geo.n, args.samples // 8 + 1, 9)
+        ref, dt = _oracle_sampled(geo, lam.cpu().numpy(), targets)
+        errs.append(float(_rel_l2_cols(out.cpu().numpy()[targets], ref).max()))
+        cpu_pairs += len(targets) * nrhs * pairs[len(errs) - 1] / geo.n
+        cpu_s += dt
+    P = sum(pairs) * nrhs
+    line = {"metric": METRIC + " [8 geometries x 8 RHS, one persistent graph-launched kernel]",
+            "value": P / med / 1e6, "unit": UNIT, "n_gpus": 1, "steps": args.ext_steps, "warmup": 3,
+            "ms_per_step": med, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batched_cylinder_plates", "n_points": [g.n for g in geos],
+                       "grids": [g.ng for g in geos], "max_occupancy": [g.meta["max_occupancy"] for g in geos],
+                       "nrhs": nrhs, "pairs_per_rhs": pairs, "work_items": batch.info["work_items"],
+                       "grid_ctas": batch.info["grid"], "plan_s": t_plan},
+            "separate_applies_ms": sep, "speedup_vs_separate_applies": sep / med,
+            "rel_l2_vs_fp64_per_geometry": errs,
+            "cpu_baseline": {"value": cpu_pairs / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.samples // 8 + 1} targets per geometry x {nrhs} RHS, {cpu_s:.1f} s "
+                                       "(pairs estimated from the mean neighbourhood; includes the oracle's binning)"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,12 +630,23 @@ def main():
     ap.add_argument("--layout", choices=("auto", "indexed", "redundant"), default="indexed")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=("sweep", "multirhs", "grad", "batched"), default="sweep",
+                    help="sweep (default): the occupancy sweep; the others measure the extension paths")
+    ap.add_argument("--scale", type=float, default=1.0, help="point-count scale of the extension workloads")
+    ap.add_argument("--ext-steps", type=int, default=20)
+    ap.add_argument("--samples", type=int, default=400, help="oracle-checked targets of the extension workloads")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: warmup raised to 3 (timing rule)", file=sys.stderr)
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "multirhs":
+        return run_multirhs(args)
+    if args.workload == "grad":
+        return run_grad(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -58,7 +58,7 @@ def load(build_if_missing: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        path = os.environ.get("P2P_LIBRARY") or _build.LIB
         if not os.path.exists(path):
             if not build_if_missing:
                 raise RuntimeError(f"libp2p.so not found at {path}")

@@ -15,7 +15,7 @@ namespace {
 
 
 template <int KERN, int R, bool RED>
-__global__ void __launch_bounds__(512) k_pair(const PairArgs a) {
+__global__ void __launch_bounds__(512, P2P_PAIR_MIN_BLOCKS) k_pair(const PairArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;

@@ -15,7 +15,19 @@
 
 #include "p2p_internal.cuh"
 
+// Unroll factor of the per-lane source loop, and the minimum number of
+// resident 512-thread blocks the pair kernel is compiled for (its register
+// budget: 65536 / (512 * P2P_PAIR_MIN_BLOCKS) registers per thread).
+#ifndef P2P_PAIR_UNROLL
+#define P2P_PAIR_UNROLL 2
+#endif
+#ifndef P2P_PAIR_MIN_BLOCKS
+#define P2P_PAIR_MIN_BLOCKS 1
+#endif
+
 namespace p2p_pair {
+
+constexpr int kPairUnroll = P2P_PAIR_UNROLL;
 
 constexpr float kInv4Pi = 0.0795774715459476679f;  // 1 / (4 pi)
 constexpr int kMaxTT = 4;
@@ -181,6 +193,7 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
         const float k = a.k;
         int s = q;
         for (; s < m_end; s += Q) pair_step<KERN, R, TT, true>(sx, sl, s, tx, acc, k);   // own box: r = 0 possible
+#pragma unroll kPairUnroll
         for (; s < ns; s += Q) pair_step<KERN, R, TT, false>(sx, sl, s, tx, acc, k);     // other boxes: r > 0
     }
 #pragma unroll
