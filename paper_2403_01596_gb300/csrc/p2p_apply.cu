@@ -13,29 +13,37 @@ using namespace p2p_pair;
 
 namespace {
 
-
-template <int KERN, int R, bool RED>
-__global__ void __launch_bounds__(512, P2P_PAIR_MIN_BLOCKS) k_pair(const PairArgs a) {
+template <int R>
+__global__ void __launch_bounds__(512, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1) k_pair(const __grid_constant__ PairArgs a,
+                                                                  unsigned long long* __restrict__ queue) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (item >= a.n_items) return;
-    process_item<KERN, R, RED>(a, item, smem_raw + (size_t)warp * warp_smem_bytes(a.chunk, R), lane);
+    unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(a.chunk, R);
+    run_pipeline<R>(ws, a.chunk, lane, [&](int ln, const PairArgs*& pa, int64_t& idx) {
+        unsigned long long v = 0;
+        if (ln == 0) v = atomicAdd(queue, 1ull);
+        v = __shfl_sync(P2P_FULL_MASK, v, 0);
+        if (v < (unsigned long long)a.n_items) {
+            pa = &a;
+            idx = (int64_t)v;
+        } else {
+            pa = nullptr;
+            idx = 0;
+        }
+    });
 }
 
 // ------------------------------------------------------ coordinate gradient --
 
-__host__ __device__ inline int grad_smem_bytes(int chunk) {
-    return chunk * 16 + chunk * 16 + chunk * 4 + 64 * 4 + 32 * kMaxTT * 16;
-}
+__host__ __device__ inline int grad_smem_bytes(int chunk) { return chunk * 16 + chunk * 16 + 32 * kMaxTT * 16; }
 
 template <int KERN, int TT>
 __device__ __forceinline__ void grad_targets(const PairArgs& a, const float4* __restrict__ sx,
                                              const float4* __restrict__ slg, float4* red, int ns, int tbase, int nt,
-                                             int rhs, int lane) {
-    const int G = (nt + TT - 1) / TT;
-    const int Q = 32 / G;
-    const int g = lane % G, q = lane / G;
+                                             int32_t map, int rhs, int lane) {
+    const int G = map_g(map), Q = map_q(map);
+    const int q = map_div(map, lane);
+    const int g = lane - q * G;
     float4 tx[TT];
     float2 tl[TT], tgv[TT];
     float acc[TT][3];
@@ -85,7 +93,8 @@ __device__ __forceinline__ void grad_targets(const PairArgs& a, const float4* __
     for (int u = 0; u < TT; ++u) red[lane * TT + u] = make_float4(acc[u][0], acc[u][1], acc[u][2], 0.f);
     __syncwarp();
     for (int t = lane; t < nt; t += 32) {
-        const int gg = t % G, u = t / G;
+        const int u = map_div(map, t);
+        const int gg = t - u * G;
         float v0 = 0.f, v1 = 0.f, v2 = 0.f;
         for (int qq = 0; qq < Q; ++qq) {
             const float4 w = red[(qq * G + gg) * TT + u];
@@ -101,8 +110,9 @@ __device__ __forceinline__ void grad_targets(const PairArgs& a, const float4* __
     __syncwarp();
 }
 
+// One warp per work item; sources gathered through the box's source list.
 template <int KERN>
-__global__ void __launch_bounds__(512) k_grad(const PairArgs a) {
+__global__ void __launch_bounds__(512) k_grad(const __grid_constant__ PairArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -111,36 +121,31 @@ __global__ void __launch_bounds__(512) k_grad(const PairArgs a) {
     unsigned char* ws = smem_raw + (size_t)warp * grad_smem_bytes(chunk);
     float4* sx = reinterpret_cast<float4*>(ws);
     float4* slg = reinterpret_cast<float4*>(ws + chunk * 16);
-    int* sj = reinterpret_cast<int*>(ws + chunk * 32);
-    int* seg = sj + chunk;
-    float4* red = reinterpret_cast<float4*>(seg + 64);
-    const int4 it = a.items[item];
-    const int b = it.x, s0 = it.y;
-    const int ns = min(chunk, a.box_src[b] - s0);
-    stage_sources<false>(a, b, s0, ns, sx, sj, seg, lane);
-    const int tb = a.box_ptr[b];
-    const int nt_all = a.box_ptr[b + 1] - tb;
+    float4* red = reinterpret_cast<float4*>(ws + chunk * 32);
+    const ItemRec r = a.items[item];
+    for (int p = lane; p < r.ns; p += 32) sx[p] = a.xs[a.nb_src[r.src_off + p]];
     for (int rhs = 0; rhs < a.nrhs; ++rhs) {
         __syncwarp();
-        for (int p = lane; p < ns; p += 32) {
-            const int64_t row = (int64_t)sj[p] * a.nrhs + rhs;
+        for (int p = lane; p < r.ns; p += 32) {
+            const int64_t row = (int64_t)a.nb_src[r.src_off + p] * a.nrhs + rhs;
             const float2 l = a.lam[row], gg = a.gsrc[row];
             slg[p] = make_float4(l.x, l.y, gg.x, gg.y);
         }
         __syncwarp();
-        for (int t0 = 0; t0 < nt_all; t0 += a.tg) {
-            const int nt = min(a.tg, nt_all - t0);
-            const int tt = choose_tt(nt, ns);
-            if (tt == 1) grad_targets<KERN, 1>(a, sx, slg, red, ns, tb + t0, nt, rhs, lane);
-            else if (tt == 2) grad_targets<KERN, 2>(a, sx, slg, red, ns, tb + t0, nt, rhs, lane);
-            else grad_targets<KERN, 4>(a, sx, slg, red, ns, tb + t0, nt, rhs, lane);
+        for (int t0 = 0; t0 < r.nt; t0 += a.tg) {
+            const int nt = min(a.tg, r.nt - t0);
+            const int32_t map = (t0 + a.tg >= r.nt) ? r.map_last : r.map_full;
+            const int tt = map_tt(map);
+            if (tt == 1) grad_targets<KERN, 1>(a, sx, slg, red, r.ns, r.tb + t0, nt, map, rhs, lane);
+            else if (tt == 2) grad_targets<KERN, 2>(a, sx, slg, red, r.ns, r.tb + t0, nt, map, rhs, lane);
+            else grad_targets<KERN, 4>(a, sx, slg, red, r.ns, r.tb + t0, nt, map, rhs, lane);
         }
     }
 }
 
 // ----------------------------------------------------------------- staging --
 
-// dst[s * nrhs + q] = src[perm[s] * ld + q]
+// dst[s * nrhs + q] = src[rows[s] * ld + q]  (rows[s] < 0: zero)
 __global__ void k_gather_rows(const float2* __restrict__ src, int64_t ld, const int32_t* __restrict__ rows, int64_t n,
                               int32_t nrhs, float2* __restrict__ dst) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -151,22 +156,36 @@ __global__ void k_gather_rows(const float2* __restrict__ src, int64_t ld, const 
     dst[i] = r >= 0 ? src[(int64_t)r * ld + q] : make_float2(0.f, 0.f);
 }
 
-template <int KERN, int R, bool RED>
-cudaError_t launch_pair(const PairArgs& a, int warps, cudaStream_t s) {
-    const int smem = warps * warp_smem_bytes(a.chunk, R);
-    auto kern = k_pair<KERN, R, RED>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+int r_index(int R) { return R == 1 ? 0 : (R == 2 ? 1 : 2); }
+
+template <int R>
+cudaError_t configure_r(const p2p_plan* p, int* grid) {
+    const int warps = p->tune.warps_per_cta;
+    const int smem = warps * warp_smem_bytes(p->tune.chunk, R);
+    cudaError_t e = cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (a.n_items + warps - 1) / warps;
-    kern<<<(unsigned)blocks, warps * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R>, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *grid = per_sm > 0 ? per_sm * sms : 0;
+    return cudaSuccess;
 }
 
-template <int KERN, bool RED>
-cudaError_t launch_pair_r(const PairArgs& a, int R, int warps, cudaStream_t s) {
-    if (R == 1) return launch_pair<KERN, 1, RED>(a, warps, s);
-    if (R == 2) return launch_pair<KERN, 2, RED>(a, warps, s);
-    return launch_pair<KERN, 4, RED>(a, warps, s);
+template <int R>
+cudaError_t launch_pair(const p2p_plan* p, const PairArgs& a, cudaStream_t s) {
+    const int warps = p->tune.warps_per_cta;
+    const int smem = warps * warp_smem_bytes(a.chunk, R);
+    int grid = p->grid[r_index(R)];
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    if ((int64_t)grid * warps > a.n_items) grid = (int)((a.n_items + warps - 1) / warps);
+    cudaError_t e = cudaMemsetAsync(p->queue, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_pair<R><<<grid, warps * 32, smem, s>>>(a, p->queue);
+    return cudaGetLastError();
 }
 
 p2p_status check_apply_args(const p2p_plan* plan, const void* lam, const void* out, int32_t nrhs, int64_t ld) {
@@ -177,6 +196,13 @@ p2p_status check_apply_args(const p2p_plan* plan, const void* lam, const void* o
 }
 
 }  // namespace
+
+cudaError_t p2p_pair_configure(p2p_plan* plan) {
+    cudaError_t e = configure_r<1>(plan, &plan->grid[0]);
+    if (e == cudaSuccess) e = configure_r<2>(plan, &plan->grid[1]);
+    if (e == cudaSuccess) e = configure_r<4>(plan, &plan->grid[2]);
+    return e;
+}
 
 // Entry shared with the tensor-core translation unit.
 p2p_status p2p_apply_tc(const p2p_plan* plan, const float2* lam_sorted, float2* out, int32_t nrhs, int64_t ld,
@@ -222,7 +248,6 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
     if (path == P2P_PATH_TC_BF16X3 && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if (path == P2P_PATH_TC_BF16X3) return p2p_apply_tc(plan, plan->lam_buf, (float2*)out, nrhs, ld, adjoint, s);
-    const bool red = plan->layout == P2P_LAYOUT_REDUNDANT;
     PairArgs a = base_args(plan);
     a.out = (float2*)out;
     a.ld = ld;
@@ -231,12 +256,7 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
     if (a.atomic_out)
         P2P_TRY_CUDA(cudaMemset2DAsync(out, (size_t)ld * 8, 0, (size_t)nrhs * 8, (size_t)plan->n, s), "p2p_apply/zero");
     const int R = path == P2P_PATH_FP32_PER_RHS ? 1 : (nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1));
-    const int warps = plan->tune.warps_per_cta;
-    cudaError_t e;
-    if (plan->kernel == P2P_HELMHOLTZ)
-        e = red ? launch_pair_r<P2P_HELMHOLTZ, true>(a, R, warps, s) : launch_pair_r<P2P_HELMHOLTZ, false>(a, R, warps, s);
-    else
-        e = red ? launch_pair_r<P2P_LAPLACE, true>(a, R, warps, s) : launch_pair_r<P2P_LAPLACE, false>(a, R, warps, s);
+    cudaError_t e = R == 1 ? launch_pair<1>(plan, a, s) : (R == 2 ? launch_pair<2>(plan, a, s) : launch_pair<4>(plan, a, s));
     P2P_TRY_CUDA(e, "p2p_apply/pair");
     return P2P_OK;
 }
@@ -276,7 +296,6 @@ P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, con
     P2P_CHECK_LAUNCH("p2p_grad_points/stage");
     P2P_TRY_CUDA(cudaMemsetAsync(grad, 0, (size_t)plan->n * 3 * sizeof(float), s), "p2p_grad_points/zero");
     PairArgs a = base_args(plan);
-    a.src_xyz = plan->xs;
     a.grad = grad;
     a.nrhs = nrhs;
     const int warps = plan->tune.warps_per_cta;

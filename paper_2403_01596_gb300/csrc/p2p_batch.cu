@@ -31,8 +31,6 @@ constexpr int kMaxBatch = 16;
 
 struct BatchGeom {
     PairArgs a;
-    int32_t kernel;
-    int32_t red;
     int64_t n;
     int64_t nrows;         // staged rows (points or packed entries)
     const int32_t* rows;   // original index of every staged row (-1: padding)
@@ -89,27 +87,26 @@ __global__ void k_batch_stage(BatchGeom* __restrict__ geoms, const BatchIO io, u
 }
 
 template <int R>
-__global__ void __launch_bounds__(512) k_pair_batched(const BatchGeom* __restrict__ geoms, const int2* __restrict__ order,
-                                                      int64_t total, unsigned long long* __restrict__ counter,
-                                                      int warp_bytes) {
+__global__ void __launch_bounds__(512, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1) k_pair_batched(const BatchGeom* __restrict__ geoms,
+                                                                          const int2* __restrict__ order, int64_t total,
+                                                                          unsigned long long* __restrict__ counter,
+                                                                          int chunk_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* ws = smem_raw + (size_t)warp * warp_bytes;
-    for (;;) {
-        unsigned long long idx = 0;
-        if (lane == 0) idx = atomicAdd(counter, 1ull);
-        idx = __shfl_sync(P2P_FULL_MASK, idx, 0);
-        if (idx >= (unsigned long long)total) break;
-        const int2 o = order[idx];
-        const BatchGeom& G = geoms[o.x];
-        if (G.kernel == P2P_HELMHOLTZ) {
-            if (G.red) process_item<P2P_HELMHOLTZ, R, true>(G.a, o.y, ws, lane);
-            else process_item<P2P_HELMHOLTZ, R, false>(G.a, o.y, ws, lane);
+    unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(chunk_max, R);
+    run_pipeline<R>(ws, chunk_max, lane, [&](int ln, const PairArgs*& pa, int64_t& idx) {
+        unsigned long long v = 0;
+        if (ln == 0) v = atomicAdd(counter, 1ull);
+        v = __shfl_sync(P2P_FULL_MASK, v, 0);
+        if (v < (unsigned long long)total) {
+            const int2 o = order[v];
+            pa = &geoms[o.x].a;
+            idx = o.y;
         } else {
-            if (G.red) process_item<P2P_LAPLACE, R, true>(G.a, o.y, ws, lane);
-            else process_item<P2P_LAPLACE, R, false>(G.a, o.y, ws, lane);
+            pa = nullptr;
+            idx = 0;
         }
-    }
+    });
 }
 
 // Sort key of every item: larger cost (targets x staged sources) first.
@@ -118,12 +115,8 @@ __global__ void k_batch_keys(const BatchGeom* __restrict__ geoms, const ItemOffs
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= off.off[off.count]) return;
     const int g = find_geom(off.off, off.count, i);
-    const PairArgs& a = geoms[g].a;
-    const int4 it = a.items[i - off.off[g]];
-    const int b = it.x;
-    const int64_t nt = a.box_ptr[b + 1] - a.box_ptr[b];
-    const int64_t ns = min(a.chunk, a.box_src[b] - it.y);
-    const uint64_t cost = (uint64_t)min(nt * ns, (int64_t)0xFFFFFFFF);
+    const ItemRec r = geoms[g].a.items[i - off.off[g]];
+    const uint64_t cost = (uint64_t)min((int64_t)r.nt * r.ns, (int64_t)0xFFFFFFFF);
     keys[i] = 0xFFFFFFFFull - cost;
     vals[i] = (int32_t)i;
 }
@@ -163,7 +156,7 @@ BatchLayout batch_layout(int64_t total, void* ws) {
 }
 
 template <int R>
-cudaError_t configure(int warps, int warp_bytes, int* ctas_per_sm) {
+cudaError_t configure(int warps, int warp_bytes, int* ctas_per_sm) {  // warp_bytes: per-warp shared memory
     const int smem = warps * warp_bytes;
     cudaError_t e = cudaFuncSetAttribute(k_pair_batched<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -178,6 +171,7 @@ struct p2p_batch {
     int32_t R;
     int32_t warps;
     int32_t warp_bytes;
+    int32_t chunk_max;
     int32_t grid;
     int64_t total;
     const p2p_plan* plans[kMaxBatch];
@@ -219,11 +213,11 @@ static p2p_status batch_launch(const p2p_batch* b, const void* const* lambdas, v
     P2P_CHECK_LAUNCH("p2p_batch_apply/stage");
     const int smem = b->warps * b->warp_bytes;
     if (b->R == 1) k_pair_batched<1><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total,
-                                                                         b->L.counter, b->warp_bytes);
+                                                                         b->L.counter, b->chunk_max);
     else if (b->R == 2) k_pair_batched<2><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total,
-                                                                              b->L.counter, b->warp_bytes);
+                                                                              b->L.counter, b->chunk_max);
     else k_pair_batched<4><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->L.counter,
-                                                               b->warp_bytes);
+                                                               b->chunk_max);
     P2P_CHECK_LAUNCH("p2p_batch_apply/pair");
     return P2P_OK;
 }
@@ -275,16 +269,15 @@ P2P_API p2p_status p2p_batch_create(p2p_batch** batch, const p2p_plan* const* pl
         b->plans[g] = p;
         host[g].a = base_args(p);
         host[g].a.nrhs = nrhs;
-        host[g].kernel = p->kernel;
-        host[g].red = p->layout == P2P_LAYOUT_REDUNDANT;
         host[g].n = p->n;
-        host[g].nrows = host[g].red ? p->packed : p->n;
-        host[g].rows = host[g].red ? p->pk_src : p->perm;
+        host[g].nrows = host[g].a.red ? p->packed : p->n;
+        host[g].rows = host[g].a.red ? p->pk_src : p->perm;
         max_chunk = std::max(max_chunk, p->tune.chunk);
         off.off[g + 1] = off.off[g] + p->n_items;
         b->io.row_off[g + 1] = b->io.row_off[g] + host[g].nrows * nrhs;
         b->io.out_off[g + 1] = b->io.out_off[g] + (host[g].a.atomic_out ? p->n * nrhs : 0);
     }
+    b->chunk_max = max_chunk;
     b->warp_bytes = warp_smem_bytes(max_chunk, b->R);
 #define FAIL(expr, where)                 \
     do {                                  \

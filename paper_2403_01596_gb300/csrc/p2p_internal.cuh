@@ -15,6 +15,45 @@ enum : unsigned int {
     P2P_DEV_TC_FAULTED = 4u    // tensor-core path bailed out (its results are not valid)
 };
 
+// One work item of the FP32 pair kernels: target box b against one chunk of
+// its concatenated neighbourhood (own box first).  Built and sorted by
+// decreasing cost (targets x sources) at plan time.
+struct ItemRec {
+    int32_t src_off;   // first entry of the chunk in the per-box source lists (pk_off[b] + chunk start)
+    int32_t ns;        // sources in the chunk
+    int32_t tb;        // first target (box-sorted index)
+    int32_t nt;        // targets of the box
+    int32_t m_end;     // the chunk's first m_end sources belong to the box itself (r = 0 possible)
+    int32_t map_full;  // lane map of a full target group (see p2p_lane_map)
+    int32_t map_last;  // lane map of the last (possibly partial) target group
+    int32_t b;         // box id
+};
+
+// Lane map of a target group of nt targets against ns sources: TT targets per
+// lane (1, 2 or 4), G = ceil(nt / TT) target slots, Q = 32 / G source slices,
+// and mG = ceil(65536 / G) so that x / G == (x * mG) >> 16 for x < 128.
+// TT minimises the lane's instruction count: ceil(ns / Q) iterations of TT
+// pair evaluations (~20 instructions each) plus the per-iteration source
+// loads and loop control (~4).  Packed as TT | G << 3 | Q << 9 | (mG - 1) << 15.
+__host__ __device__ inline int32_t p2p_lane_map(int nt, int ns) {
+    int best = 4, best_cost = 0x7fffffff;
+    for (int tt = 1; tt <= 4; tt <<= 1) {
+        const int g = (nt + tt - 1) / tt;
+        if (g > 32 || g < 1) continue;
+        const int q = 32 / g;
+        const int cost = (20 * tt + 4) * ((ns + q - 1) / q);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = tt;
+        }
+    }
+    int g = (nt + best - 1) / best;
+    if (g < 1) g = 1;
+    const int q = 32 / g;
+    const int mg = (65536 + g - 1) / g;
+    return best | (g << 3) | (q << 9) | ((mg - 1) << 15);
+}
+
 struct p2p_plan {
     // sizes and parameters
     int64_t n;
@@ -36,14 +75,16 @@ struct p2p_plan {
     // carved from the caller's workspace
     float4* xs;             // [n] box-sorted coordinates (w = 0)
     int32_t* box_src;       // [nb] S_b, sources in the neighbourhood of box b
-    int32_t* box_self;      // [nb] position of box b's own sources inside its concatenated neighbourhood
-    int4* items;            // [n_items] (box, source begin, target begin, 0)
+    ItemRec* items;         // [n_items] work items, heaviest first
     int64_t n_items;
     int32_t max_chunks;     // max over boxes of ceil(S_b / chunk)
     int32_t max_box;        // largest box occupancy
-    int32_t* pk_off;        // [nb + 1] packed offsets (redundant layout)
-    float4* pk_xyz;         // [packed] per-box neighbourhood coordinates
-    int32_t* pk_src;        // [packed] original index of each packed source, -1 for padding
+    int32_t* pk_off;        // [nb + 1] offsets of the per-box source lists (each padded to 4 entries)
+    int32_t* nb_src;        // [packed] box-sorted index of every listed source, -1 for padding
+    float4* pk_xyz;         // [packed] redundant layout: per-box copy of the listed coordinates
+    int32_t* pk_src;        // [packed] redundant layout: original index of every listed source, -1 for padding
+    unsigned long long* queue;  // work-queue counter of the persistent pair kernel
+    int32_t grid[3];        // persistent grid of the pair kernel for R = 1, 2, 4 right-hand sides per pass
     float2* lam_buf;        // [max(n, packed) * max_nrhs] sorted / packed strengths
     float2* g_buf;          // [n * max_nrhs] sorted upstream gradient (coordinate gradient)
     unsigned int* status;   // device status word
@@ -84,6 +125,10 @@ cudaError_t radix_sort_pairs(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, 
                              int bits, void* work, cudaStream_t s, bool* result_in_alt);
 
 }  // namespace p2p_detail
+
+// Persistent grid sizes of the pair kernel for the plan's kernel, layout and
+// tuning (resident blocks per SM x SMs), one per right-hand-side block width.
+cudaError_t p2p_pair_configure(p2p_plan* plan);
 
 #define P2P_TRY_CUDA(expr, where)                        \
     do {                                                 \

@@ -1,16 +1,30 @@
 // Device code of the FP32 pair kernel shared by the per-plan launch
 // (p2p_apply.cu) and the persistent batched launch (p2p_batch.cu).
 //
-// Work decomposition.  A work item is one target box b and one chunk of at
-// most `chunk` sources of b's concatenated neighbourhood.  One warp owns one
-// item: it stages the chunk's coordinates and strengths into its own
-// shared-memory region and then sweeps every target of b against them.
-// Inside the warp a target group of nt <= 128 targets is mapped to lanes as
-// (g, q): lane g + q*G holds TT targets {g, g+G, ...} (G = ceil(nt/TT)) and the
-// q-th of Q = 32/G interleaved slices of the chunk, so the idle-lane fraction
-// stays small for any box occupancy; slice partials are combined through
-// shared memory.  Items of boxes with more than one chunk add into the zeroed
-// output with float2 atomics; single-chunk plans store directly.
+// Work.  A work item (ItemRec, built at plan time and sorted heaviest first)
+// is one target box against one chunk of at most `chunk` entries of the box's
+// source list: the box's own sources first, then those of its other neighbour
+// boxes in ascending id.  The indexed layout (Sec. 3.2) lists box-sorted
+// indices and gathers coordinates and strengths through them; the redundant
+// layout (Sec. 3.3) holds a per-box copy of the coordinates and a per-apply
+// repack of the strengths, so a chunk is one contiguous tile.
+//
+// Pipeline.  The kernel is persistent: every warp takes items from a global
+// queue (atomic counter) and keeps two shared-memory stages.  While it sweeps
+// the targets of item i against stage i % 2, the sources of item i + 1 are
+// already on their way into the other stage -- with cp.async (per-lane 16/8 B
+// asynchronous copies) for the indexed gather, or with one or two TMA bulk
+// copies (cp.async.bulk, completion on an mbarrier) for the redundant tile.
+// Waits on an mbarrier are bounded; on expiry the warp sets the status word,
+// drains its copies (bounded) and stops.
+//
+// Lanes.  A target group of nt <= 128 targets is mapped to lanes as (g, q):
+// lane g + q*G holds TT targets {g, g + G, ...} (G = ceil(nt / TT)) and sweeps
+// the q-th of Q = 32 / G interleaved slices of the chunk; the slice partials
+// are combined through shared memory.  The map (TT, G, Q and a reciprocal for
+// the divisions by G) is precomputed per item.  Items of boxes with more than
+// one chunk add into the zeroed output with float2 atomics; single-chunk
+// plans store directly.
 #pragma once
 
 #include "p2p_internal.cuh"
@@ -22,115 +36,144 @@
 #define P2P_PAIR_UNROLL 2
 #endif
 #ifndef P2P_PAIR_MIN_BLOCKS
-#define P2P_PAIR_MIN_BLOCKS 1
+#define P2P_PAIR_MIN_BLOCKS 2
 #endif
 
 namespace p2p_pair {
 
 constexpr int kPairUnroll = P2P_PAIR_UNROLL;
-
 constexpr float kInv4Pi = 0.0795774715459476679f;  // 1 / (4 pi)
 constexpr int kMaxTT = 4;
+constexpr uint32_t kBulkWaitLimit = 1u << 24;
 
 struct PairArgs {
-    const int4* items;
+    const ItemRec* items;
     int64_t n_items;
-    const float4* xs;       // box-sorted coordinates (targets, and sources of the indexed layout)
-    const float4* src_xyz;  // sources: xs (indexed) or the packed tiles (redundant)
+    const float4* xs;       // box-sorted coordinates (targets; indexed sources)
+    const float4* pk_xyz;   // redundant layout: per-box source tiles
+    const int32_t* nb_src;  // per-box source lists (box-sorted indices)
     const float2* lam;      // staged strengths, row stride nrhs: sorted (indexed) or packed (redundant)
     const float2* gsrc;     // staged upstream gradient (coordinate gradient only), row stride nrhs
-    const int32_t* box_ptr;
-    const int32_t* nbr_ptr;
-    const int32_t* nbr_idx;
-    const int32_t* box_src;
-    const int32_t* pk_off;
     const int32_t* perm;
     float2* out;
     float* grad;
+    unsigned int* status;
     int64_t ld;
     int32_t nrhs;
     float k;
     int32_t chunk;
     int32_t tg;
     int32_t atomic_out;
+    int32_t kernel;
+    int32_t red;
 };
 
+// Per-warp shared memory: two stages (coordinates + R strengths per source),
+// the slice-reduction buffer and two mbarriers.
+__host__ __device__ inline int stage_bytes(int chunk, int R) { return chunk * 16 + chunk * R * 8; }
 __host__ __device__ inline int warp_smem_bytes(int chunk, int R) {
-    // coords + strengths (R per source) + staged source index + segment table + reduction
-    return chunk * 16 + chunk * R * 8 + chunk * 4 + 64 * 4 + 32 * kMaxTT * R * 8;
+    return 2 * stage_bytes(chunk, R) + 32 * kMaxTT * R * 8 + 16;
 }
 
-// Stages the coordinates of sources [s0, s0 + ns) of box b's neighbourhood and
-// records, for each, the row of the strength arrays it reads.  The
-// neighbourhood is concatenated with the box's own sources first (its n_b
-// sources occupy positions [0, n_b)), then the other neighbour boxes in
-// ascending id; only the own box can hold r = 0 pairs.  The redundant layout
-// packs its tiles in the same order.
-template <bool RED>
-__device__ __forceinline__ void stage_sources(const PairArgs& a, int b, int s0, int ns, float4* sx, int* sj, int* seg,
-                                              int lane) {
-    if (RED) {
-        const int base = a.pk_off[b] + s0;
-        for (int p = lane; p < ns; p += 32) {
-            sj[p] = base + p;
-            sx[p] = a.src_xyz[base + p];
+// ------------------------------------------------------------ async copies --
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_addr(bar);
+    for (uint32_t i = 0; i < kBulkWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ stages --
+
+struct Stage {
+    float4* sx;  // chunk coordinates
+    float2* sl;  // chunk * R strengths
+};
+
+__device__ __forceinline__ Stage stage_at(unsigned char* ws, int chunk, int R, int i) {
+    unsigned char* b = ws + i * stage_bytes(chunk, R);
+    return Stage{reinterpret_cast<float4*>(b), reinterpret_cast<float2*>(b + chunk * 16)};
+}
+
+// Starts the copies of item `r` into stage `st`.  Strengths travel with the
+// coordinates only when one pass covers all right-hand sides (nrhs == R).
+template <int R>
+__device__ __forceinline__ void issue_stage(const PairArgs& a, const ItemRec& r, const Stage& st, uint64_t* bar,
+                                            int lane) {
+    const bool lam_async = a.nrhs == R;
+    if (a.red) {
+        if (lane == 0) {
+            // the stage was last read through the generic proxy; order those reads before the bulk write
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const uint32_t n4 = (uint32_t)((r.ns + 3) & ~3);
+            const uint32_t bytes = n4 * 16u + (lam_async ? n4 * (uint32_t)R * 8u : 0u);
+            mbar_expect_tx(bar, bytes);
+            bulk_g2s(st.sx, a.pk_xyz + r.src_off, n4 * 16u, bar);
+            if (lam_async) bulk_g2s(st.sl, a.lam + (int64_t)r.src_off * R, n4 * (uint32_t)R * 8u, bar);
         }
     } else {
-        const int e0 = a.nbr_ptr[b];
-        const int ne = a.nbr_ptr[b + 1] - e0;
-        const int c = lane < ne ? a.nbr_idx[e0 + lane] : -1;
-        const unsigned selfm = __ballot_sync(P2P_FULL_MASK, c == b);
-        const int sp = selfm ? __ffs(selfm) - 1 : 0;
-        // slot 0 <- the own box, slots 1..sp <- entries 0..sp-1, later slots unchanged
-        const int from = lane == 0 ? sp : (lane <= sp ? lane - 1 : lane);
-        const int cs = __shfl_sync(P2P_FULL_MASK, c, from);
-        int start = 0, len = 0;
-        if (lane < ne) {
-            start = a.box_ptr[cs];
-            len = a.box_ptr[cs + 1] - start;
-        }
-        int incl = len;
+        for (int p = lane; p < r.ns; p += 32) {
+            const int j = a.nb_src[r.src_off + p];
+            cp_async16(st.sx + p, a.xs + j);
+            if (lam_async) {
+                if (R == 1) cp_async8(st.sl + p, a.lam + j);
+                else {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(P2P_FULL_MASK, incl, o);
-            if (lane >= o) incl += y;
-        }
-        seg[lane] = incl - len;     // exclusive prefix: first concatenated position of slot lane
-        seg[32 + lane] = start;     // first sorted index of slot lane
-        __syncwarp();
-        for (int p = lane; p < ns; p += 32) {
-            const int pp = s0 + p;
-            int lo = 0, hi = ne - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (seg[mid] <= pp) lo = mid;
-                else hi = mid - 1;
+                    for (int h = 0; h < R; h += 2) cp_async16(st.sl + p * R + h, a.lam + (int64_t)j * R + h);
+                }
             }
-            const int j = seg[32 + lo] + (pp - seg[lo]);
-            sj[p] = j;
-            sx[p] = a.xs[j];
         }
+        cp_async_commit();
     }
 }
 
-// Chooses targets-per-lane TT in {1, 2, 4} minimising the lane's instruction
-// count: ceil(ns / Q) iterations of TT pair evaluations (~20 instructions
-// each) plus the per-iteration source loads and loop control (~4).
-__device__ __forceinline__ int choose_tt(int nt, int ns) {
-    int best = 4, best_cost = 0x7fffffff;
+// Strengths of right-hand sides [rb, rb + R) for the staged chunk (the
+// synchronous path used when nrhs > R).
+template <int R>
+__device__ __forceinline__ void load_lam_block(const PairArgs& a, const ItemRec& r, float2* sl, int rb, int lane) {
+    for (int p = lane; p < r.ns; p += 32) {
+        const int64_t row = (int64_t)(a.red ? r.src_off + p : a.nb_src[r.src_off + p]) * a.nrhs + rb;
 #pragma unroll
-    for (int tt = 1; tt <= 4; tt <<= 1) {
-        const int g = (nt + tt - 1) / tt;
-        if (g > 32) continue;
-        const int q = 32 / g;
-        const int cost = (20 * tt + 4) * ((ns + q - 1) / q);
-        if (cost < best_cost) {
-            best_cost = cost;
-            best = tt;
-        }
+        for (int q = 0; q < R; ++q) sl[p * R + q] = (rb + q < a.nrhs) ? a.lam[row + q] : make_float2(0.f, 0.f);
     }
-    return best;
 }
+
+// ------------------------------------------------------------------- sweep --
 
 // One staged source against the lane's TT targets.  MASK: the source may
 // coincide with a target (own box) and r = 0 pairs are skipped; otherwise r > 0
@@ -172,14 +215,19 @@ __device__ __forceinline__ void pair_step(const float4* __restrict__ sx, const f
     }
 }
 
+__device__ __forceinline__ int map_tt(int32_t m) { return m & 7; }
+__device__ __forceinline__ int map_g(int32_t m) { return (m >> 3) & 63; }
+__device__ __forceinline__ int map_q(int32_t m) { return (m >> 9) & 63; }
+__device__ __forceinline__ int map_div(int32_t m, int x) { return (x * ((int)(((uint32_t)m) >> 15) + 1)) >> 16; }
+
 // Sweeps the staged chunk for one target group and writes / adds the results.
 template <int KERN, int R, int TT>
 __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* __restrict__ sx,
                                               const float2* __restrict__ sl, float2* red, int ns, int m_end,
-                                              int tbase, int nt, int rb, int lane) {
-    const int G = (nt + TT - 1) / TT;
-    const int Q = 32 / G;
-    const int g = lane % G, q = lane / G;
+                                              int tbase, int nt, int32_t map, int rb, int lane) {
+    const int G = map_g(map), Q = map_q(map);
+    const int q = map_div(map, lane);
+    const int g = lane - q * G;
     float4 tx[TT];
     float2 acc[TT][R];
 #pragma unroll
@@ -192,9 +240,9 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
     if (q < Q) {
         const float k = a.k;
         int s = q;
-        for (; s < m_end; s += Q) pair_step<KERN, R, TT, true>(sx, sl, s, tx, acc, k);   // own box: r = 0 possible
+        for (; s < m_end; s += Q) pair_step<KERN, R, TT, true>(sx, sl, s, tx, acc, k);  // own box: r = 0 possible
 #pragma unroll kPairUnroll
-        for (; s < ns; s += Q) pair_step<KERN, R, TT, false>(sx, sl, s, tx, acc, k);     // other boxes: r > 0
+        for (; s < ns; s += Q) pair_step<KERN, R, TT, false>(sx, sl, s, tx, acc, k);    // other boxes: r > 0
     }
 #pragma unroll
     for (int u = 0; u < TT; ++u)
@@ -202,7 +250,8 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
         for (int r = 0; r < R; ++r) red[(lane * TT + u) * R + r] = acc[u][r];
     __syncwarp();
     for (int t = lane; t < nt; t += 32) {
-        const int gg = t % G, u = t / G;
+        const int u = map_div(map, t);
+        const int gg = t - u * G;
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = make_float2(0.f, 0.f);
@@ -228,42 +277,91 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
     __syncwarp();
 }
 
-// Processes one work item (target box, source chunk) with the calling warp:
-// stage the chunk into the warp's shared-memory region `ws`, then sweep every
-// target group of the box against it for every block of R right-hand sides.
-template <int KERN, int R, bool RED>
-__device__ __forceinline__ void process_item(const PairArgs& a, int64_t item, unsigned char* ws, int lane) {
-    const int chunk = a.chunk;
-    float4* sx = reinterpret_cast<float4*>(ws);
-    float2* sl = reinterpret_cast<float2*>(ws + chunk * 16);
-    int* sj = reinterpret_cast<int*>(ws + chunk * 16 + chunk * R * 8);
-    int* seg = sj + chunk;
-    float2* red = reinterpret_cast<float2*>(seg + 64);
-
-    const int4 it = a.items[item];
-    const int b = it.x, s0 = it.y;
-    const int ns = min(chunk, a.box_src[b] - s0);
-    stage_sources<RED>(a, b, s0, ns, sx, sj, seg, lane);
-    const int tb = a.box_ptr[b];
-    const int nt_all = a.box_ptr[b + 1] - tb;
-    const int m_end = max(0, min(ns, nt_all - s0));  // own-box sources of this chunk come first
+// Sweeps every target group of item `r` against its staged chunk, for every
+// block of R right-hand sides.
+template <int KERN, int R>
+__device__ __forceinline__ void compute_item(const PairArgs& a, const ItemRec& r, const Stage& st, float2* red,
+                                             int lane) {
     for (int rb = 0; rb < a.nrhs; rb += R) {
-        __syncwarp();
-        for (int p = lane; p < ns; p += 32) {
-            const int64_t row = (int64_t)sj[p] * a.nrhs + rb;
-#pragma unroll
-            for (int r = 0; r < R; ++r) sl[p * R + r] = (rb + r < a.nrhs) ? a.lam[row + r] : make_float2(0.f, 0.f);
+        if (a.nrhs != R) {
+            __syncwarp();
+            load_lam_block<R>(a, r, st.sl, rb, lane);
+            __syncwarp();
         }
-        __syncwarp();
-        for (int t0 = 0; t0 < nt_all; t0 += a.tg) {
-            const int nt = min(a.tg, nt_all - t0);
-            const int tt = choose_tt(nt, ns);
-            if (tt == 1) sweep_targets<KERN, R, 1>(a, sx, sl, red, ns, m_end, tb + t0, nt, rb, lane);
-            else if (tt == 2) sweep_targets<KERN, R, 2>(a, sx, sl, red, ns, m_end, tb + t0, nt, rb, lane);
-            else sweep_targets<KERN, R, 4>(a, sx, sl, red, ns, m_end, tb + t0, nt, rb, lane);
+        for (int t0 = 0; t0 < r.nt; t0 += a.tg) {
+            const int nt = min(a.tg, r.nt - t0);
+            const int32_t map = (t0 + a.tg >= r.nt) ? r.map_last : r.map_full;
+            const int tt = map_tt(map);
+            if (tt == 1) sweep_targets<KERN, R, 1>(a, st.sx, st.sl, red, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
+            else if (tt == 2) sweep_targets<KERN, R, 2>(a, st.sx, st.sl, red, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
+            else sweep_targets<KERN, R, 4>(a, st.sx, st.sl, red, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
         }
     }
+}
+
+template <int R>
+__device__ __forceinline__ void compute_dispatch(const PairArgs& a, const ItemRec& r, const Stage& st, float2* red,
+                                                 int lane) {
+    if (a.kernel == P2P_HELMHOLTZ) compute_item<P2P_HELMHOLTZ, R>(a, r, st, red, lane);
+    else compute_item<P2P_LAPLACE, R>(a, r, st, red, lane);
+}
+
+// The per-warp pipeline.  `next(lane)` returns the next work item as
+// (args pointer, item index) or a null args pointer when the queue is empty;
+// it is called by the whole warp and must return the same value in every lane.
+template <int R, typename Next>
+__device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int lane, Next next) {
+    const int sb = 2 * stage_bytes(chunk, R);
+    float2* red = reinterpret_cast<float2*>(ws + sb);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ws + sb + 32 * kMaxTT * R * 8);
+    if (lane == 0) {
+        mbar_init(&bars[0]);
+        mbar_init(&bars[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncwarp();
+    uint32_t parity[2] = {0u, 0u};
+    const PairArgs* ca;
+    int64_t ci;
+    next(lane, ca, ci);
+    if (!ca) return;
+    ItemRec cr = ca->items[ci];
+    int cur = 0;
+    issue_stage<R>(*ca, cr, stage_at(ws, chunk, R, cur), &bars[cur], lane);
+    for (;;) {
+        const PairArgs* na;
+        int64_t ni;
+        next(lane, na, ni);
+        ItemRec nr;
+        if (na) {
+            nr = na->items[ni];
+            issue_stage<R>(*na, nr, stage_at(ws, chunk, R, cur ^ 1), &bars[cur ^ 1], lane);
+        }
+        // wait for the current stage
+        bool ok = true;
+        if (ca->red) {
+            ok = mbar_wait(&bars[cur], parity[cur]);
+            parity[cur] ^= 1u;
+        } else {
+            if (na && !na->red) cp_async_wait<1>();
+            else cp_async_wait<0>();
+        }
+        __syncwarp();
+        if (!__all_sync(P2P_FULL_MASK, ok)) {
+            if (lane == 0) atomicOr(ca->status, P2P_DEV_TIMEOUT);
+            // drain: the copies of the next stage, if any (bounded), and any cp.async group
+            if (na && na->red) mbar_wait(&bars[cur ^ 1], parity[cur ^ 1]);
+            cp_async_wait<0>();
+            return;
+        }
+        compute_dispatch<R>(*ca, cr, stage_at(ws, chunk, R, cur), red, lane);
+        __syncwarp();
+        if (!na) break;
+        ca = na;
+        ci = ni;
+        cr = nr;
+        cur ^= 1;
+    }
 }
 
 inline PairArgs base_args(const p2p_plan* p) {
@@ -271,23 +369,22 @@ inline PairArgs base_args(const p2p_plan* p) {
     a.items = p->items;
     a.n_items = p->n_items;
     a.xs = p->xs;
-    a.src_xyz = p->layout == P2P_LAYOUT_REDUNDANT ? p->pk_xyz : p->xs;
+    a.pk_xyz = p->pk_xyz;
+    a.nb_src = p->nb_src;
     a.lam = p->lam_buf;
     a.gsrc = p->g_buf;
-    a.box_ptr = p->box_ptr;
-    a.nbr_ptr = p->nbr_ptr;
-    a.nbr_idx = p->nbr_idx;
-    a.box_src = p->box_src;
-    a.pk_off = p->pk_off;
     a.perm = p->perm;
     a.out = nullptr;
     a.grad = nullptr;
+    a.status = p->status;
     a.ld = 0;
     a.nrhs = 1;
     a.k = p->k;
     a.chunk = p->tune.chunk;
     a.tg = p->tune.target_group;
     a.atomic_out = p->max_chunks > 1;
+    a.kernel = p->kernel;
+    a.red = p->layout == P2P_LAYOUT_REDUNDANT;
     return a;
 }
 

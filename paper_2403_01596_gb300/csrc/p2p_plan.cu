@@ -157,12 +157,11 @@ __global__ void k_gather_xyz(const float* __restrict__ pts, const int32_t* __res
     xs[s] = make_float4(pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], 0.f);
 }
 
-// Per box: S_b, position of the own box inside the concatenated neighbourhood,
-// work-item count ceil(S_b / chunk) and padded packed size.  Validates the CSR.
+// Per box: S_b, work-item count ceil(S_b / chunk) and the padded length of its
+// source list.  Validates the CSR (ascending ids in range, own box present).
 __global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ nbr_ptr,
                            const int32_t* __restrict__ nbr_idx, int32_t nb, int64_t nnz, int chunk,
-                           int32_t* __restrict__ box_src, int32_t* __restrict__ box_self,
-                           int32_t* __restrict__ n_chunks, int32_t* __restrict__ padded, int32_t* __restrict__ maxes,
+                           int32_t* __restrict__ box_src, int32_t* __restrict__ n_chunks, int32_t* __restrict__ padded, int32_t* __restrict__ maxes,
                            unsigned int* __restrict__ status) {
     int32_t b = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (b >= nb) return;
@@ -187,7 +186,6 @@ __global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* _
         self = 0;
     }
     box_src[b] = (int32_t)s;
-    box_self[b] = (int32_t)self;
     int32_t c = (int32_t)((s + chunk - 1) / chunk);
     n_chunks[b] = c;
     padded[b] = (int32_t)((s + 3) & ~3ll);
@@ -195,21 +193,49 @@ __global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* _
     atomicMax(&maxes[1], own);
 }
 
-__global__ void k_items(const int32_t* __restrict__ n_chunks, const int32_t* __restrict__ item_off, int32_t nb,
-                        int chunk, int4* __restrict__ items) {
+// Work-item records (unsorted) and their sort keys: larger cost (targets x
+// sources) first.
+__global__ void k_item_records(const int32_t* __restrict__ n_chunks, const int32_t* __restrict__ item_off,
+                               const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ box_src,
+                               const int32_t* __restrict__ pk_off, int32_t nb, int chunk, int tg,
+                               ItemRec* __restrict__ recs, uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
     int32_t b = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (b >= nb) return;
-    int32_t c = n_chunks[b], o = item_off[b];
-    for (int32_t i = 0; i < c; ++i) items[o + i] = make_int4(b, i * chunk, 0, 0);
+    const int32_t c = n_chunks[b], o = item_off[b];
+    const int32_t tb = box_ptr[b], nt = box_ptr[b + 1] - tb, S = box_src[b];
+    const int32_t last = nt - ((nt - 1) / tg) * tg;  // targets of the last target group
+    for (int32_t i = 0; i < c; ++i) {
+        const int32_t s0 = i * chunk;
+        ItemRec r;
+        r.src_off = pk_off[b] + s0;
+        r.ns = min(chunk, S - s0);
+        r.tb = tb;
+        r.nt = nt;
+        r.m_end = max(0, min(r.ns, nt - s0));
+        r.map_full = p2p_lane_map(min(nt, tg), r.ns);
+        r.map_last = p2p_lane_map(last, r.ns);
+        r.b = b;
+        recs[o + i] = r;
+        keys[o + i] = 0xFFFFFFFFull - (uint64_t)min((int64_t)nt * r.ns, (int64_t)0xFFFFFFFF);
+        vals[o + i] = o + i;
+    }
 }
 
-// One warp per box: copy the neighbourhood's sources into the box's packed
-// tile, the box's own sources first, then the other neighbour boxes in
-// ascending id (the order the pair kernel's r = 0 mask relies on).
+__global__ void k_item_gather(const ItemRec* __restrict__ recs, const int32_t* __restrict__ order, int64_t n,
+                              ItemRec* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = recs[order[i]];
+}
+
+// One warp per box: writes the box's source list -- the box's own sources
+// first, then the other neighbour boxes in ascending id (the order the pair
+// kernel's r = 0 mask relies on) -- as box-sorted indices (nb_src, the index
+// arrays of the indexing method, Sec. 3.2) and, for the redundant layout, as a
+// copy of the coordinates plus original indices (the repetition of Sec. 3.3).
 __global__ void k_pack(const float4* __restrict__ xs, const int32_t* __restrict__ perm,
                        const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ nbr_ptr,
                        const int32_t* __restrict__ nbr_idx, const int32_t* __restrict__ pk_off, int32_t nb,
-                       float4* __restrict__ pk_xyz, int32_t* __restrict__ pk_src) {
+                       int32_t* __restrict__ nb_src, float4* __restrict__ pk_xyz, int32_t* __restrict__ pk_src) {
     const int lane = threadIdx.x & 31;
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
@@ -245,11 +271,17 @@ __global__ void k_pack(const float4* __restrict__ xs, const int32_t* __restrict_
         const int32_t x0 = __shfl_sync(P2P_FULL_MASK, excl, seg);
         if (p < total) {
             const int32_t j = s0 + (p - x0);
-            pk_xyz[base + p] = xs[j];
-            pk_src[base + p] = perm[j];
+            nb_src[base + p] = j;
+            if (pk_xyz) {
+                pk_xyz[base + p] = xs[j];
+                pk_src[base + p] = perm[j];
+            }
         } else if (p < padded) {
-            pk_xyz[base + p] = make_float4(0.f, 0.f, 0.f, 0.f);
-            pk_src[base + p] = -1;
+            nb_src[base + p] = -1;
+            if (pk_xyz) {
+                pk_xyz[base + p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                pk_src[base + p] = -1;
+            }
         }
     }
 }
@@ -346,6 +378,11 @@ struct PlanLayout {
     p2p_plan p;  // pointers only
     int32_t *n_chunks, *item_off, *padded, *maxes, *small;
     void* scan_ws;
+    // item-sort scratch (aliases the strength staging buffer when it is large enough)
+    ItemRec* recs;
+    uint64_t *keys, *keys_alt;
+    int32_t *vals, *vals_alt;
+    void* radix_ws;
     size_t bytes;
 };
 
@@ -356,17 +393,20 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, p2p_layout layout
     memset(&L.p, 0, sizeof(L.p));
     size_t m = (size_t)(n > 0 ? n : 1), mb = (size_t)(nb > 0 ? nb : 1);
     const size_t max_items = (size_t)(sources / t.chunk) + mb + 1;
-    const size_t packed_bound = layout == P2P_LAYOUT_REDUNDANT ? (size_t)sources + 3 * mb + 4 : 0;
+    const size_t list_bound = (size_t)sources + 3 * mb + 4;
+    const bool red = layout == P2P_LAYOUT_REDUNDANT;
     L.p.status = c.take<unsigned int>(4);
     L.p.scratch64 = c.take<long long>(4);
+    L.p.queue = c.take<unsigned long long>(2);
     L.p.xs = c.take<float4>(m);
     L.p.box_src = c.take<int32_t>(mb);
-    L.p.box_self = c.take<int32_t>(mb);
-    L.p.items = c.take<int4>(max_items);
+    L.p.items = c.take<ItemRec>(max_items);
     L.p.pk_off = c.take<int32_t>(mb + 1);
-    L.p.pk_xyz = c.take<float4>(packed_bound ? packed_bound : 1);
-    L.p.pk_src = c.take<int32_t>(packed_bound ? packed_bound : 1);
-    const size_t lam_rows = m > packed_bound ? m : packed_bound;
+    L.p.nb_src = c.take<int32_t>(list_bound);
+    L.p.pk_xyz = red ? c.take<float4>(list_bound) : nullptr;
+    L.p.pk_src = red ? c.take<int32_t>(list_bound) : nullptr;
+    const size_t lam_rows = red ? (m > list_bound ? m : list_bound) : m;
+    const size_t lam_bytes = lam_rows * (size_t)max_nrhs * sizeof(float2);
     L.p.lam_buf = c.take<float2>(lam_rows * (size_t)max_nrhs);
     L.p.g_buf = c.take<float2>(m * (size_t)max_nrhs);
     L.n_chunks = c.take<int32_t>(mb);
@@ -375,6 +415,22 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, p2p_layout layout
     L.maxes = c.take<int32_t>(4);
     L.small = c.take<int32_t>(4);
     L.scan_ws = c.take<char>(scan_workspace_bytes(nb));
+    // sort scratch: inside lam_buf if it fits, else after everything else
+    Carver sc{reinterpret_cast<char*>(L.p.lam_buf), 0, lam_bytes};
+    sc.take<ItemRec>(max_items);
+    sc.take<uint64_t>(max_items);
+    sc.take<uint64_t>(max_items);
+    sc.take<int32_t>(max_items);
+    sc.take<int32_t>(max_items);
+    sc.take<char>(radix_workspace_bytes((int64_t)max_items));
+    Carver& cs = (sc.off <= lam_bytes) ? sc : c;
+    if (&cs == &sc) sc.off = 0;
+    L.recs = cs.take<ItemRec>(max_items);
+    L.keys = cs.take<uint64_t>(max_items);
+    L.keys_alt = cs.take<uint64_t>(max_items);
+    L.vals = cs.take<int32_t>(max_items);
+    L.vals_alt = cs.take<int32_t>(max_items);
+    L.radix_ws = cs.take<char>(radix_workspace_bytes((int64_t)max_items));
     L.bytes = align_up(c.off, 256);
     return L;
 }
@@ -570,31 +626,40 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
     k_gather_xyz<<<blocks_for(n, kThreads), kThreads, 0, s>>>(pts, perm, n, p->xs);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/gather");
     k_box_info<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(box_ptr, nbr_ptr, nbr_idx, num_boxes, nnz,
-                                                                     t.chunk, p->box_src, p->box_self, L.n_chunks,
-                                                                     L.padded, L.maxes, p->status);
+                                                                     t.chunk, p->box_src, L.n_chunks, L.padded,
+                                                                     L.maxes, p->status);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/box_info");
     FAIL_CUDA(scan_exclusive_i32(L.n_chunks, L.item_off, num_boxes, L.small, L.scan_ws, s), "p2p_plan_create/scan");
-    k_items<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(L.n_chunks, L.item_off, num_boxes, t.chunk,
-                                                                 p->items);
+    FAIL_CUDA(scan_exclusive_i32(L.padded, p->pk_off, num_boxes, p->pk_off + num_boxes, L.scan_ws, s),
+              "p2p_plan_create/scan_lists");
+    k_pack<<<blocks_for((int64_t)num_boxes * 32, kThreads), kThreads, 0, s>>>(
+        p->xs, perm, box_ptr, nbr_ptr, nbr_idx, p->pk_off, num_boxes, p->nb_src, p->pk_xyz, p->pk_src);
+    FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/pack");
+    k_item_records<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(L.n_chunks, L.item_off, box_ptr, p->box_src,
+                                                                        p->pk_off, num_boxes, t.chunk, t.target_group,
+                                                                        L.recs, L.keys, L.vals);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/items");
-    if (layout == P2P_LAYOUT_REDUNDANT) {
-        FAIL_CUDA(scan_exclusive_i32(L.padded, p->pk_off, num_boxes, p->pk_off + num_boxes, L.scan_ws, s),
-                  "p2p_plan_create/scan_packed");
-        k_pack<<<blocks_for((int64_t)num_boxes * 32, kThreads), kThreads, 0, s>>>(
-            p->xs, perm, box_ptr, nbr_ptr, nbr_idx, p->pk_off, num_boxes, p->pk_xyz, p->pk_src);
-        FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/pack");
-    }
     int32_t host[4] = {0, 0, 0, 0};
     unsigned int status = 0;
     int32_t packed = 0;
     FAIL_CUDA(cudaMemcpyAsync(host, L.maxes, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
     FAIL_CUDA(cudaMemcpyAsync(host + 2, L.small, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
     FAIL_CUDA(cudaMemcpyAsync(&status, p->status, sizeof(status), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
-    if (layout == P2P_LAYOUT_REDUNDANT)
-        FAIL_CUDA(cudaMemcpyAsync(&packed, p->pk_off + num_boxes, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
-                  "p2p_plan_create");
+    FAIL_CUDA(cudaMemcpyAsync(&packed, p->pk_off + num_boxes, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+              "p2p_plan_create");
     FAIL_CUDA(cudaStreamSynchronize(s), "p2p_plan_create");
-#undef FAIL_CUDA
+    if (!status) {
+        const int64_t items = host[2];
+        bool in_alt = false;
+        FAIL_CUDA(radix_sort_pairs(L.keys, L.vals, L.keys_alt, L.vals_alt, items, 32, L.radix_ws, s, &in_alt),
+                  "p2p_plan_create/sort");
+        if (items > 0) {
+            k_item_gather<<<blocks_for(items, kThreads), kThreads, 0, s>>>(L.recs, in_alt ? L.vals_alt : L.vals,
+                                                                           items, p->items);
+            FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/order");
+        }
+        FAIL_CUDA(cudaStreamSynchronize(s), "p2p_plan_create");
+    }
     if (status) {
         free(p);
         return P2P_ERR_INVALID;
