@@ -158,16 +158,25 @@ __global__ void k_gather_rows(const float2* __restrict__ src, int64_t ld, const 
 
 int r_index(int R) { return R == 1 ? 0 : (R == 2 ? 1 : 2); }
 
+// The dynamic shared-memory limit is an attribute of the kernel function,
+// shared by every plan: it is raised once to the device's opt-in maximum so
+// that no plan's configuration can lower it below another plan's launch.
 template <int R>
 cudaError_t configure_r(const p2p_plan* p, int* grid) {
     const int warps = p->tune.warps_per_cta;
     const int smem = warps * warp_smem_bytes(p->tune.chunk, R);
-    cudaError_t e = cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0, dev = 0, sms = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > optin) {
+        *grid = 0;
+        return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R>, warps * 32, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;

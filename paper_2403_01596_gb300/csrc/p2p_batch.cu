@@ -155,10 +155,22 @@ BatchLayout batch_layout(int64_t total, void* ws) {
     return L;
 }
 
+// warp_bytes: per-warp shared memory.  The kernel's dynamic shared-memory
+// limit is raised once to the device's opt-in maximum (the attribute is shared
+// by every batch).
 template <int R>
-cudaError_t configure(int warps, int warp_bytes, int* ctas_per_sm) {  // warp_bytes: per-warp shared memory
+cudaError_t configure(int warps, int warp_bytes, int* ctas_per_sm) {
     const int smem = warps * warp_bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_pair_batched<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > optin) {
+        *ctas_per_sm = 0;
+        return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(k_pair_batched<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_pair_batched<R>, warps * 32, smem);
 }
