@@ -159,22 +159,35 @@ __global__ void k_gather_rows(const float2* __restrict__ src, int64_t ld, const 
 int r_index(int R) { return R == 1 ? 0 : (R == 2 ? 1 : 2); }
 
 // The dynamic shared-memory limit is an attribute of the kernel function,
-// shared by every plan: it is raised once to the device's opt-in maximum so
-// that no plan's configuration can lower it below another plan's launch.
+// shared by every plan: it only ever grows (to the largest launch seen), so no
+// plan's configuration can lower it below another plan's launch.
+int g_smem_attr[3] = {0, 0, 0};
+
+template <int R>
+cudaError_t raise_smem_limit(int smem) {
+    int& cur = g_smem_attr[r_index(R)];
+    if (smem <= __atomic_load_n(&cur, __ATOMIC_ACQUIRE)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) {
+        int seen = __atomic_load_n(&cur, __ATOMIC_ACQUIRE);
+        while (seen < smem && !__atomic_compare_exchange_n(&cur, &seen, smem, false, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE)) {
+        }
+    }
+    return e;
+}
+
 template <int R>
 cudaError_t configure_r(const p2p_plan* p, int* grid) {
     const int warps = p->tune.warps_per_cta;
     const int smem = warps * warp_smem_bytes(p->tune.chunk, R);
     int per_sm = 0, dev = 0, sms = 0, optin = 0;
+    *grid = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if (smem > optin) {
-        *grid = 0;
-        return cudaSuccess;
-    }
-    e = cudaFuncSetAttribute(k_pair<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (smem > optin) return cudaSuccess;  // this right-hand-side width does not fit with this tuning
+    e = raise_smem_limit<R>(smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R>, warps * 32, smem);
     if (e != cudaSuccess) return e;
@@ -185,16 +198,20 @@ cudaError_t configure_r(const p2p_plan* p, int* grid) {
 }
 
 template <int R>
-cudaError_t launch_pair(const p2p_plan* p, const PairArgs& a, cudaStream_t s) {
+p2p_status launch_pair(const p2p_plan* p, const PairArgs& a, cudaStream_t s) {
     const int warps = p->tune.warps_per_cta;
     const int smem = warps * warp_smem_bytes(a.chunk, R);
     int grid = p->grid[r_index(R)];
-    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    if (grid <= 0) {
+        set_message("p2p_apply: the pair kernel does not fit on this device with this tuning (shared memory)");
+        return P2P_ERR_UNSUPPORTED;
+    }
     if ((int64_t)grid * warps > a.n_items) grid = (int)((a.n_items + warps - 1) / warps);
-    cudaError_t e = cudaMemsetAsync(p->queue, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
+    P2P_TRY_CUDA(raise_smem_limit<R>(smem), "p2p_apply/attribute");
+    P2P_TRY_CUDA(cudaMemsetAsync(p->queue, 0, sizeof(unsigned long long), s), "p2p_apply/queue");
     k_pair<R><<<grid, warps * 32, smem, s>>>(a, p->queue);
-    return cudaGetLastError();
+    P2P_CHECK_LAUNCH("p2p_apply/pair");
+    return P2P_OK;
 }
 
 p2p_status check_apply_args(const p2p_plan* plan, const void* lam, const void* out, int32_t nrhs, int64_t ld) {
@@ -265,9 +282,7 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
     if (a.atomic_out)
         P2P_TRY_CUDA(cudaMemset2DAsync(out, (size_t)ld * 8, 0, (size_t)nrhs * 8, (size_t)plan->n, s), "p2p_apply/zero");
     const int R = path == P2P_PATH_FP32_PER_RHS ? 1 : (nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1));
-    cudaError_t e = R == 1 ? launch_pair<1>(plan, a, s) : (R == 2 ? launch_pair<2>(plan, a, s) : launch_pair<4>(plan, a, s));
-    P2P_TRY_CUDA(e, "p2p_apply/pair");
-    return P2P_OK;
+    return R == 1 ? launch_pair<1>(plan, a, s) : (R == 2 ? launch_pair<2>(plan, a, s) : launch_pair<4>(plan, a, s));
 }
 
 P2P_API p2p_status p2p_apply_path(const p2p_plan* plan, const void* lambda, void* out, int32_t nrhs, int64_t ld,
