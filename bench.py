@@ -267,9 +267,8 @@ def run_ours(args):
     from paper_2403_01596_gb300 import _capi as C
     from paper_2403_01596_gb300 import api, workloads as W
 
-    world = _env_int("WORLD_SIZE", 1)
-    rank = _env_int("RANK", 0)
-    local = _env_int("LOCAL_RANK", 0)
+    from paper_2403_01596_gb300 import replicas
+    rank, local, world = replicas.world()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -336,8 +335,7 @@ def run_ours(args):
     clocks = ClockSampler(bus)
     clocks.start()
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for s in range(args.steps):
@@ -346,19 +344,14 @@ def run_ours(args):
             one_apply(i, evs[s][i])
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    if dist:
-        dist.barrier()
+    replicas.barrier()
     clk = clocks.stop()
     step_ms = [evs[s][0][0].elapsed_time(evs[s][nd - 1][2]) for s in range(args.steps)]
     pair_ms = [[evs[s][i][1].elapsed_time(evs[s][i][2]) for s in range(args.steps)] for i in range(nd)]
     stage_ms = [[evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps)] for i in range(nd)]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / args.steps
-    value = world * step_pairs / (ms_per_step * 1e-3) / 1e9
+    value = replicas.job_throughput(step_pairs, world, ms_per_step * 1e-3) / 1e9
 
     # ---------------- end to end through the public API with host buffers
     host_lam = [lam.cpu().pin_memory() for lam in lams]

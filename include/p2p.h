@@ -339,6 +339,15 @@ P2P_API p2p_status p2p_batch_destroy(p2p_batch* batch);
 P2P_API p2p_status p2p_diag_tc_gemm(const float* A, const float* B, float* D, int32_t K, int32_t n,
                                     unsigned int* status, p2p_stream_t stream);
 
+/*
+ * Self-check of the bounded waits (not part of the operator): one warp waits
+ * on an mbarrier that nothing arrives at, with the poll loop of the pipelined
+ * kernels capped at `limit` polls (>= 1).  The wait runs out, bit 1
+ * (P2P_ERR_TIMEOUT's device flag) is set in *status [dev], the kernel returns
+ * and the CUDA context remains usable.
+ */
+P2P_API p2p_status p2p_diag_wait_timeout(unsigned int* status, int32_t limit, p2p_stream_t stream);
+
 /* Reads and clears the plan's device status word.  Synchronises. */
 P2P_API p2p_status p2p_last_async_status(const p2p_plan* plan, p2p_stream_t stream);
 

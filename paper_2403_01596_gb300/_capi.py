@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
             "p2p_grad_points": ([P, P, P, P, i32, i64, P], ctypes.c_int),
             "p2p_last_async_status": ([P, P], ctypes.c_int),
             "p2p_diag_tc_gemm": ([P, P, P, i32, i32, P, P], ctypes.c_int),
+            "p2p_diag_wait_timeout": ([P, i32, P], ctypes.c_int),
             "p2p_batch_workspace_size": ([P, i32, i32, PSZ], ctypes.c_int),
             "p2p_batch_create": ([ctypes.POINTER(P), P, i32, i32, i32, P, sz, P], ctypes.c_int),
             "p2p_batch_apply": ([P, P, P, i64, P], ctypes.c_int),
@@ -296,3 +297,7 @@ def p2p_batch_info(batch) -> dict:
 def p2p_batch_destroy(batch):
     if batch:
         load().p2p_batch_destroy(batch)
+
+
+def p2p_diag_wait_timeout(status, limit, stream=None):
+    check(load().p2p_diag_wait_timeout(_ptr(status), int(limit), _stream(stream)), "p2p_diag_wait_timeout")

@@ -668,6 +668,8 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
     p->max_box = host[1];
     p->n_items = host[2];
     p->packed = packed;
+    FAIL_CUDA(p2p_pair_configure(p), "p2p_plan_create/occupancy");
+#undef FAIL_CUDA
     *plan = p;
     return P2P_OK;
 }
