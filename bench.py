@@ -236,6 +236,8 @@ def run_reference(args):
 def _config(args, layout):
     return {"workload": "sphere_occupancy_sweep", "n_points": 1 << 20, "occupancies": list(OCCUPANCIES),
             "grids": [180, 124, 86, 61], "kernel": "helmholtz", "k": "2*pi/(4h)", "nrhs": 1, "layout": layout,
+            "tuning": {"chunk": getattr(args, "chunk", 0), "warps_per_cta": getattr(args, "warps", 0),
+                       "target_group": getattr(args, "target_group", 0)},
             "l2": "flushed between timed steps (256 MiB write, outside the timed events)"}
 
 
@@ -293,7 +295,8 @@ def run_ours(args):
             tune = autotune.best_config(wl, pts)
             layout, tuning = tune["layout"], tune["tuning"]
         else:
-            tuning = None
+            tuning = {k: v for k, v in (("chunk", args.chunk), ("warps_per_cta", args.warps),
+                                        ("target_group", args.target_group)) if v} or None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         plan = api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k, layout=layout, tuning=tuning)
@@ -621,6 +624,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--layout", choices=("auto", "indexed", "redundant"), default="indexed")
+    ap.add_argument("--chunk", type=int, default=0, help="sources per work item (0: library default)")
+    ap.add_argument("--warps", type=int, default=0, help="warps per block (0: library default)")
+    ap.add_argument("--target-group", type=int, default=0, help="targets per sweep (0: library default)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=("sweep", "multirhs", "grad", "batched"), default="sweep",

@@ -13,24 +13,16 @@ using namespace p2p_pair;
 
 namespace {
 
+// Persistent pair kernel: warp w of the grid takes items w, w + W, w + 2W, ...
+// of the plan's heaviest-first item list (W = warps in the grid).
 template <int R>
-__global__ void __launch_bounds__(512, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1) k_pair(const __grid_constant__ PairArgs a,
-                                                                  unsigned long long* __restrict__ queue) {
+__global__ void __launch_bounds__(512, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1) k_pair(const __grid_constant__ PairArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
     unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(a.chunk, R);
-    run_pipeline<R>(ws, a.chunk, lane, [&](int ln, const PairArgs*& pa, int64_t& idx) {
-        unsigned long long v = 0;
-        if (ln == 0) v = atomicAdd(queue, 1ull);
-        v = __shfl_sync(P2P_FULL_MASK, v, 0);
-        if (v < (unsigned long long)a.n_items) {
-            pa = &a;
-            idx = (int64_t)v;
-        } else {
-            pa = nullptr;
-            idx = 0;
-        }
-    });
+    run_pipeline<R>(ws, a.chunk, lane, a.items, a.n_items, (int64_t)blockIdx.x * warps + warp,
+                    (int64_t)gridDim.x * warps, a.status, [&](const ItemRec&) -> const PairArgs& { return a; });
 }
 
 // ------------------------------------------------------ coordinate gradient --
@@ -208,8 +200,7 @@ p2p_status launch_pair(const p2p_plan* p, const PairArgs& a, cudaStream_t s) {
     }
     if ((int64_t)grid * warps > a.n_items) grid = (int)((a.n_items + warps - 1) / warps);
     P2P_TRY_CUDA(raise_smem_limit<R>(smem), "p2p_apply/attribute");
-    P2P_TRY_CUDA(cudaMemsetAsync(p->queue, 0, sizeof(unsigned long long), s), "p2p_apply/queue");
-    k_pair<R><<<grid, warps * 32, smem, s>>>(a, p->queue);
+    k_pair<R><<<grid, warps * 32, smem, s>>>(a);
     P2P_CHECK_LAUNCH("p2p_apply/pair");
     return P2P_OK;
 }

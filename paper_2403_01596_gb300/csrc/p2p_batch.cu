@@ -9,12 +9,12 @@
 //                   outputs that are accumulated with atomics and resets the
 //                   work-queue counter;
 //   k_pair_batched  a persistent grid (resident blocks x SMs) whose warps take
-//                   work items (geometry, box, source chunk) from one global
-//                   queue with an atomic counter; the queue is ordered by
-//                   decreasing item cost (targets x sources), so the heaviest
-//                   boxes of the most crowded geometry start first and the
-//                   small ones fill the tail.  A warp leaves when the counter
-//                   passes the end; there is no waiting on other warps.
+//                   work items (geometry, box, source chunk) from one combined
+//                   list ordered by decreasing item cost (targets x sources),
+//                   warp w taking items w, w + W, ... (W warps), so the
+//                   heaviest boxes of the most crowded geometry start first and
+//                   the small ones fill the tail.  Warps never wait on each
+//                   other.
 // The per-item work is the same device code as the per-plan pair kernel.
 #include <string.h>
 
@@ -88,25 +88,14 @@ __global__ void k_batch_stage(BatchGeom* __restrict__ geoms, const BatchIO io, u
 
 template <int R>
 __global__ void __launch_bounds__(512, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1) k_pair_batched(const BatchGeom* __restrict__ geoms,
-                                                                          const int2* __restrict__ order, int64_t total,
-                                                                          unsigned long long* __restrict__ counter,
-                                                                          int chunk_max) {
+                                                                                         const ItemRec* __restrict__ recs,
+                                                                                         int64_t total, int chunk_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
     unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(chunk_max, R);
-    run_pipeline<R>(ws, chunk_max, lane, [&](int ln, const PairArgs*& pa, int64_t& idx) {
-        unsigned long long v = 0;
-        if (ln == 0) v = atomicAdd(counter, 1ull);
-        v = __shfl_sync(P2P_FULL_MASK, v, 0);
-        if (v < (unsigned long long)total) {
-            const int2 o = order[v];
-            pa = &geoms[o.x].a;
-            idx = o.y;
-        } else {
-            pa = nullptr;
-            idx = 0;
-        }
-    });
+    run_pipeline<R>(ws, chunk_max, lane, recs, total, (int64_t)blockIdx.x * warps + warp, (int64_t)gridDim.x * warps,
+                    geoms[0].a.status, [&](const ItemRec& r) -> const PairArgs& { return geoms[r.b].a; });
 }
 
 // Sort key of every item: larger cost (targets x staged sources) first.
@@ -121,17 +110,21 @@ __global__ void k_batch_keys(const BatchGeom* __restrict__ geoms, const ItemOffs
     vals[i] = (int32_t)i;
 }
 
-__global__ void k_batch_order(const int32_t* __restrict__ sorted, const ItemOffsets off, int2* __restrict__ order) {
+// Combined item list in cost order; the record's last field names its geometry.
+__global__ void k_batch_order(const BatchGeom* __restrict__ geoms, const int32_t* __restrict__ sorted,
+                              const ItemOffsets off, ItemRec* __restrict__ recs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= off.off[off.count]) return;
     const int64_t v = sorted[i];
     const int g = find_geom(off.off, off.count, v);
-    order[i] = make_int2(g, (int)(v - off.off[g]));
+    ItemRec r = geoms[g].a.items[v - off.off[g]];
+    r.b = g;
+    recs[i] = r;
 }
 
 struct BatchLayout {
     BatchGeom* geoms;
-    int2* order;
+    ItemRec* order;
     unsigned long long* counter;
     uint64_t *keys, *keys_alt;
     int32_t *vals, *vals_alt;
@@ -144,7 +137,7 @@ BatchLayout batch_layout(int64_t total, void* ws) {
     BatchLayout L;
     size_t m = (size_t)(total > 0 ? total : 1);
     L.geoms = c.take<BatchGeom>(kMaxBatch);
-    L.order = c.take<int2>(m);
+    L.order = c.take<ItemRec>(m);
     L.counter = c.take<unsigned long long>(1);
     L.keys = c.take<uint64_t>(m);
     L.keys_alt = c.take<uint64_t>(m);
@@ -224,12 +217,12 @@ static p2p_status batch_launch(const p2p_batch* b, const void* const* lambdas, v
     k_batch_stage<<<(unsigned)blocks, threads, 0, s>>>(b->L.geoms, io, b->L.counter);
     P2P_CHECK_LAUNCH("p2p_batch_apply/stage");
     const int smem = b->warps * b->warp_bytes;
-    if (b->R == 1) k_pair_batched<1><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total,
-                                                                         b->L.counter, b->chunk_max);
-    else if (b->R == 2) k_pair_batched<2><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total,
-                                                                              b->L.counter, b->chunk_max);
-    else k_pair_batched<4><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->L.counter,
-                                                               b->chunk_max);
+    if (b->R == 1)
+        k_pair_batched<1><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->chunk_max);
+    else if (b->R == 2)
+        k_pair_batched<2><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->chunk_max);
+    else
+        k_pair_batched<4><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->chunk_max);
     P2P_CHECK_LAUNCH("p2p_batch_apply/pair");
     return P2P_OK;
 }
@@ -319,7 +312,7 @@ P2P_API p2p_status p2p_batch_create(p2p_batch** batch, const p2p_plan* const* pl
     bool in_alt = false;
     FAIL(radix_sort_pairs(L.keys, L.vals, L.keys_alt, L.vals_alt, total, 32, L.radix_ws, s, &in_alt),
          "p2p_batch_create/sort");
-    k_batch_order<<<blocks, 256, 0, s>>>(in_alt ? L.vals_alt : L.vals, off, L.order);
+    k_batch_order<<<blocks, 256, 0, s>>>(L.geoms, in_alt ? L.vals_alt : L.vals, off, L.order);
     FAIL(cudaGetLastError(), "p2p_batch_create/order");
     FAIL(cudaStreamSynchronize(s), "p2p_batch_create");
 #undef FAIL

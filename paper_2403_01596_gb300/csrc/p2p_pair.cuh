@@ -68,11 +68,12 @@ struct PairArgs {
     int32_t red;
 };
 
-// Per-warp shared memory: two stages (coordinates + R strengths per source),
-// the slice-reduction buffer and two mbarriers.
+// Per-warp shared memory: two data stages (coordinates + R strengths per
+// source), two index stages (the chunk's source list, indexed layout), the
+// slice-reduction buffer and four mbarriers (two for data, two for indices).
 __host__ __device__ inline int stage_bytes(int chunk, int R) { return chunk * 16 + chunk * R * 8; }
 __host__ __device__ inline int warp_smem_bytes(int chunk, int R) {
-    return 2 * stage_bytes(chunk, R) + 32 * kMaxTT * R * 8 + 16;
+    return 2 * stage_bytes(chunk, R) + 2 * chunk * 4 + 32 * kMaxTT * R * 8 + 32;
 }
 
 // ------------------------------------------------------------ async copies --
@@ -125,16 +126,47 @@ struct Stage {
     float2* sl;  // chunk * R strengths
 };
 
-__device__ __forceinline__ Stage stage_at(unsigned char* ws, int chunk, int R, int i) {
-    unsigned char* b = ws + i * stage_bytes(chunk, R);
-    return Stage{reinterpret_cast<float4*>(b), reinterpret_cast<float2*>(b + chunk * 16)};
+struct WarpSmem {
+    unsigned char* data;  // two data stages
+    int* idx;             // two index stages of `chunk` ints
+    float2* red;
+    uint64_t* bar;        // bar[0..1]: data stages, bar[2..3]: index stages
+    int chunk;
+    int R;
+    __device__ __forceinline__ Stage stage(int i) const {
+        unsigned char* b = data + i * stage_bytes(chunk, R);
+        return Stage{reinterpret_cast<float4*>(b), reinterpret_cast<float2*>(b + chunk * 16)};
+    }
+    __device__ __forceinline__ int* index(int i) const { return idx + i * chunk; }
+};
+
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char* ws, int chunk, int R) {
+    WarpSmem w;
+    w.chunk = chunk;
+    w.R = R;
+    w.data = ws;
+    w.idx = reinterpret_cast<int*>(ws + 2 * stage_bytes(chunk, R));
+    w.red = reinterpret_cast<float2*>(ws + 2 * stage_bytes(chunk, R) + 2 * chunk * 4);
+    w.bar = reinterpret_cast<uint64_t*>(ws + 2 * stage_bytes(chunk, R) + 2 * chunk * 4 + 32 * kMaxTT * R * 8);
+    return w;
 }
 
-// Starts the copies of item `r` into stage `st`.  Strengths travel with the
-// coordinates only when one pass covers all right-hand sides (nrhs == R).
+// Indexed layout, two items ahead: one TMA bulk copy of the chunk's source
+// list (box-sorted indices) into index stage `i` (lane 0 only).
+__device__ __forceinline__ void issue_index_copy(const PairArgs& a, const ItemRec& r, const WarpSmem& w, int i) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const uint32_t n4 = (uint32_t)((r.ns + 3) & ~3);
+    mbar_expect_tx(&w.bar[2 + i], n4 * 4u);
+    bulk_g2s(w.index(i), a.nb_src + r.src_off, n4 * 4u, &w.bar[2 + i]);
+}
+
+// One item ahead: the chunk's coordinates and (when one pass covers every
+// right-hand side, nrhs == R) strengths into data stage `i`.  Redundant: two
+// TMA bulk copies of the contiguous tile (lane 0).  Indexed: per-lane cp.async
+// gathers through the index stage `i`, which the caller has waited for.
 template <int R>
-__device__ __forceinline__ void issue_stage(const PairArgs& a, const ItemRec& r, const Stage& st, uint64_t* bar,
-                                            int lane) {
+__device__ __forceinline__ void issue_data(const PairArgs& a, const ItemRec& r, const WarpSmem& w, int i, int lane) {
+    const Stage st = w.stage(i);
     const bool lam_async = a.nrhs == R;
     if (a.red) {
         if (lane == 0) {
@@ -142,13 +174,14 @@ __device__ __forceinline__ void issue_stage(const PairArgs& a, const ItemRec& r,
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             const uint32_t n4 = (uint32_t)((r.ns + 3) & ~3);
             const uint32_t bytes = n4 * 16u + (lam_async ? n4 * (uint32_t)R * 8u : 0u);
-            mbar_expect_tx(bar, bytes);
-            bulk_g2s(st.sx, a.pk_xyz + r.src_off, n4 * 16u, bar);
-            if (lam_async) bulk_g2s(st.sl, a.lam + (int64_t)r.src_off * R, n4 * (uint32_t)R * 8u, bar);
+            mbar_expect_tx(&w.bar[i], bytes);
+            bulk_g2s(st.sx, a.pk_xyz + r.src_off, n4 * 16u, &w.bar[i]);
+            if (lam_async) bulk_g2s(st.sl, a.lam + (int64_t)r.src_off * R, n4 * (uint32_t)R * 8u, &w.bar[i]);
         }
     } else {
+        const int* idx = w.index(i);
         for (int p = lane; p < r.ns; p += 32) {
-            const int j = a.nb_src[r.src_off + p];
+            const int j = idx[p];
             cp_async16(st.sx + p, a.xs + j);
             if (lam_async) {
                 if (R == 1) cp_async8(st.sl + p, a.lam + j);
@@ -158,8 +191,8 @@ __device__ __forceinline__ void issue_stage(const PairArgs& a, const ItemRec& r,
                 }
             }
         }
-        cp_async_commit();
     }
+    cp_async_commit();  // one group per item and lane, possibly empty
 }
 
 // Strengths of right-hand sides [rb, rb + R) for the staged chunk (the
@@ -247,7 +280,7 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
 #pragma unroll
     for (int u = 0; u < TT; ++u)
 #pragma unroll
-        for (int r = 0; r < R; ++r) red[(lane * TT + u) * R + r] = acc[u][r];
+        for (int r = 0; r < R; ++r) red[(u * 32 + lane) * R + r] = acc[u][r];
     __syncwarp();
     for (int t = lane; t < nt; t += 32) {
         const int u = map_div(map, t);
@@ -259,7 +292,7 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
             const int l2 = qq * G + gg;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const float2 w = red[(l2 * TT + u) * R + r];
+                const float2 w = red[(u * 32 + l2) * R + r];
                 v[r].x += w.x;
                 v[r].y += w.y;
             }
@@ -306,61 +339,107 @@ __device__ __forceinline__ void compute_dispatch(const PairArgs& a, const ItemRe
     else compute_item<P2P_LAPLACE, R>(a, r, st, red, lane);
 }
 
-// The per-warp pipeline.  `next(lane)` returns the next work item as
-// (args pointer, item index) or a null args pointer when the queue is empty;
-// it is called by the whole warp and must return the same value in every lane.
-template <int R, typename Next>
-__device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int lane, Next next) {
-    const int sb = 2 * stage_bytes(chunk, R);
-    float2* red = reinterpret_cast<float2*>(ws + sb);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(ws + sb + 32 * kMaxTT * R * 8);
+// Item record distributed over lanes 0..7 of a warp (field f in lane f).
+__device__ __forceinline__ int32_t load_rec_lane(const ItemRec* items, int64_t idx, int64_t n, int lane) {
+    return (idx < n && lane < 8) ? reinterpret_cast<const int32_t*>(items + idx)[lane] : 0;
+}
+
+__device__ __forceinline__ ItemRec gather_rec(int32_t v) {
+    ItemRec r;
+    r.src_off = __shfl_sync(P2P_FULL_MASK, v, 0);
+    r.ns = __shfl_sync(P2P_FULL_MASK, v, 1);
+    r.tb = __shfl_sync(P2P_FULL_MASK, v, 2);
+    r.nt = __shfl_sync(P2P_FULL_MASK, v, 3);
+    r.m_end = __shfl_sync(P2P_FULL_MASK, v, 4);
+    r.map_full = __shfl_sync(P2P_FULL_MASK, v, 5);
+    r.map_last = __shfl_sync(P2P_FULL_MASK, v, 6);
+    r.b = __shfl_sync(P2P_FULL_MASK, v, 7);
+    return r;
+}
+
+// The per-warp pipeline over the items first, first + stride, ... of `items`
+// (n of them).  `args_of(rec)` gives the PairArgs an item belongs to.  At the
+// top of iteration k the warp holds records k .. k+2 (lane-distributed) and
+// starts loading record k+3; it issues the index copy of item k+2 (indexed
+// layout) and the data copies of item k+1, then waits for item k's data and
+// sweeps it.  Every mbarrier wait is bounded.
+template <int R, typename ArgsOf>
+__device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int lane, const ItemRec* items, int64_t n,
+                                             int64_t first, int64_t stride, unsigned int* status, ArgsOf args_of) {
+    const WarpSmem w = warp_smem(ws, chunk, R);
     if (lane == 0) {
-        mbar_init(&bars[0]);
-        mbar_init(&bars[1]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mbar_init(&w.bar[i]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
-    uint32_t parity[2] = {0u, 0u};
-    const PairArgs* ca;
-    int64_t ci;
-    next(lane, ca, ci);
-    if (!ca) return;
-    ItemRec cr = ca->items[ci];
-    int cur = 0;
-    issue_stage<R>(*ca, cr, stage_at(ws, chunk, R, cur), &bars[cur], lane);
-    for (;;) {
-        const PairArgs* na;
-        int64_t ni;
-        next(lane, na, ni);
-        ItemRec nr;
-        if (na) {
-            nr = na->items[ni];
-            issue_stage<R>(*na, nr, stage_at(ws, chunk, R, cur ^ 1), &bars[cur ^ 1], lane);
+    if (first >= n) return;
+    uint32_t parity[4] = {0u, 0u, 0u, 0u};
+    bool failed = false;
+    // prologue: records 0..2, index copies of items 0 and 1, data of item 0
+    int32_t v0 = load_rec_lane(items, first, n, lane);
+    int32_t v1 = load_rec_lane(items, first + stride, n, lane);
+    int32_t v2 = load_rec_lane(items, first + 2 * stride, n, lane);
+    ItemRec r0 = gather_rec(v0), r1 = gather_rec(v1);
+    const bool has1 = first + stride < n;
+    const PairArgs* a0 = &args_of(r0);
+    const PairArgs* a1 = has1 ? &args_of(r1) : nullptr;
+    if (lane == 0) {
+        if (!a0->red) issue_index_copy(*a0, r0, w, 0);
+        if (a1 && !a1->red) issue_index_copy(*a1, r1, w, 1);
+    }
+    if (!a0->red) {
+        failed |= !mbar_wait(&w.bar[2], parity[2]);
+        parity[2] ^= 1u;
+    }
+    failed = !__all_sync(P2P_FULL_MASK, !failed);
+    if (!failed) issue_data<R>(*a0, r0, w, 0, lane);
+    int64_t k = 0;
+    while (!failed) {
+        const int cur = (int)(k & 1), nxt = cur ^ 1;
+        const int64_t i1 = first + (k + 1) * stride, i2 = first + (k + 2) * stride, i3 = first + (k + 3) * stride;
+        const int32_t v3 = load_rec_lane(items, i3, n, lane);  // consumed two iterations later
+        const ItemRec r2 = gather_rec(v2);
+        const PairArgs* a2 = i2 < n ? &args_of(r2) : nullptr;
+        // index copy of item k+2 into index stage cur (item k's indices are no longer needed)
+        if (a2 && !a2->red && lane == 0) issue_index_copy(*a2, r2, w, cur);
+        // data of item k+1
+        if (a1) {
+            if (!a1->red) {
+                failed |= !mbar_wait(&w.bar[2 + nxt], parity[2 + nxt]);
+                parity[2 + nxt] ^= 1u;
+                failed = !__all_sync(P2P_FULL_MASK, !failed);
+                if (failed) break;
+            }
+            issue_data<R>(*a1, r1, w, nxt, lane);
         }
-        // wait for the current stage
-        bool ok = true;
-        if (ca->red) {
-            ok = mbar_wait(&bars[cur], parity[cur]);
+        // wait for item k's data
+        if (a0->red) {
+            failed |= !mbar_wait(&w.bar[cur], parity[cur]);
             parity[cur] ^= 1u;
-        } else {
-            if (na && !na->red) cp_async_wait<1>();
-            else cp_async_wait<0>();
         }
+        if (a1) cp_async_wait<1>();
+        else cp_async_wait<0>();
         __syncwarp();
-        if (!__all_sync(P2P_FULL_MASK, ok)) {
-            if (lane == 0) atomicOr(ca->status, P2P_DEV_TIMEOUT);
-            // drain: the copies of the next stage, if any (bounded), and any cp.async group
-            if (na && na->red) mbar_wait(&bars[cur ^ 1], parity[cur ^ 1]);
-            cp_async_wait<0>();
-            return;
-        }
-        compute_dispatch<R>(*ca, cr, stage_at(ws, chunk, R, cur), red, lane);
+        failed = !__all_sync(P2P_FULL_MASK, !failed);
+        if (failed) break;
+        compute_dispatch<R>(*a0, r0, w.stage(cur), w.red, lane);
         __syncwarp();
-        if (!na) break;
-        ca = na;
-        ci = ni;
-        cr = nr;
-        cur ^= 1;
+        if (!a1) break;
+        r0 = r1;
+        a0 = a1;
+        r1 = r2;
+        a1 = a2;
+        v2 = v3;
+        ++k;
+        (void)i1;
+    }
+    if (failed) {
+        if (lane == 0) atomicOr(status, P2P_DEV_TIMEOUT);
+        // drain every bulk copy that may still be in flight (bounded), then the cp.async groups
+        for (int i = 0; i < 4; ++i) mbar_wait(&w.bar[i], parity[i], 1u << 20);
+        cp_async_wait<0>();
+        __syncwarp();
     }
 }
 
