@@ -148,6 +148,41 @@ __global__ void k_gather_rows(const float2* __restrict__ src, int64_t ld, const 
     dst[i] = r >= 0 ? src[(int64_t)r * ld + q] : make_float2(0.f, 0.f);
 }
 
+// One right-hand side, four rows per thread: dst[s] = src[rows[s] * ld]
+// (rows[s] < 0: zero) with a 16-byte index load, four independent gathers
+// and two 16-byte stores.  rows and dst are 16-byte aligned.
+__global__ void k_gather_rows4(const float2* __restrict__ src, int64_t ld, const int32_t* __restrict__ rows, int64_t n,
+                               float2* __restrict__ dst) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s0 = q * 4;
+    if (s0 >= n) return;
+    if (s0 + 4 <= n) {
+        const int4 r = *reinterpret_cast<const int4*>(rows + s0);
+        const float2 z = make_float2(0.f, 0.f);
+        const float2 v0 = r.x >= 0 ? src[(int64_t)r.x * ld] : z;
+        const float2 v1 = r.y >= 0 ? src[(int64_t)r.y * ld] : z;
+        const float2 v2 = r.z >= 0 ? src[(int64_t)r.z * ld] : z;
+        const float2 v3 = r.w >= 0 ? src[(int64_t)r.w * ld] : z;
+        reinterpret_cast<float4*>(dst + s0)[0] = make_float4(v0.x, v0.y, v1.x, v1.y);
+        reinterpret_cast<float4*>(dst + s0)[1] = make_float4(v2.x, v2.y, v3.x, v3.y);
+    } else {
+        for (int64_t s = s0; s < n; ++s) dst[s] = rows[s] >= 0 ? src[(int64_t)rows[s] * ld] : make_float2(0.f, 0.f);
+    }
+}
+
+cudaError_t stage_rows(const float2* src, int64_t ld, const int32_t* rows, int64_t nrows, int32_t nrhs, float2* dst,
+                       cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    if (nrhs == 1) {
+        const int64_t threads = (nrows + 3) / 4;
+        k_gather_rows4<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(src, ld, rows, nrows, dst);
+    } else {
+        const int64_t total = nrows * nrhs;
+        k_gather_rows<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(src, ld, rows, nrows, nrhs, dst);
+    }
+    return cudaGetLastError();
+}
+
 int r_index(int R) { return R == 1 ? 0 : (R == 2 ? 1 : 2); }
 
 // The dynamic shared-memory limit is an attribute of the kernel function,
@@ -169,29 +204,38 @@ cudaError_t raise_smem_limit(int smem) {
 }
 
 template <int R>
-cudaError_t configure_r(const p2p_plan* p, int* grid) {
-    const int warps = p->tune.warps_per_cta;
-    const int smem = warps * warp_smem_bytes(p->tune.chunk, R);
-    int per_sm = 0, dev = 0, sms = 0, optin = 0;
-    *grid = 0;
+cudaError_t configure_r(p2p_plan* p) {
+    const int ri = r_index(R);
+    p->grid[ri] = 0;
+    p->grid_warps[ri] = 0;
+    int dev = 0, sms = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if (smem > optin) return cudaSuccess;  // this right-hand-side width does not fit with this tuning
-    e = raise_smem_limit<R>(smem);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R>, warps * 32, smem);
-    if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    *grid = per_sm > 0 ? per_sm * sms : 0;
-    return cudaSuccess;
+    // the tuning's warps per block, halved until one block's shared memory fits
+    for (int warps = p->tune.warps_per_cta; warps >= 1; warps >>= 1) {
+        const int smem = warps * warp_smem_bytes(p->tune.chunk, R);
+        if (smem > optin) continue;
+        e = raise_smem_limit<R>(smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R>, warps * 32, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm > 0) {
+            p->grid[ri] = per_sm * sms;
+            p->grid_warps[ri] = warps;
+            return cudaSuccess;
+        }
+    }
+    return cudaSuccess;  // no block fits: the launch reports P2P_ERR_UNSUPPORTED
 }
 
 template <int R>
 p2p_status launch_pair(const p2p_plan* p, const PairArgs& a, cudaStream_t s) {
-    const int warps = p->tune.warps_per_cta;
+    const int warps = p->grid_warps[r_index(R)];
     const int smem = warps * warp_smem_bytes(a.chunk, R);
     int grid = p->grid[r_index(R)];
     if (grid <= 0) {
@@ -215,9 +259,9 @@ p2p_status check_apply_args(const p2p_plan* plan, const void* lam, const void* o
 }  // namespace
 
 cudaError_t p2p_pair_configure(p2p_plan* plan) {
-    cudaError_t e = configure_r<1>(plan, &plan->grid[0]);
-    if (e == cudaSuccess) e = configure_r<2>(plan, &plan->grid[1]);
-    if (e == cudaSuccess) e = configure_r<4>(plan, &plan->grid[2]);
+    cudaError_t e = configure_r<1>(plan);
+    if (e == cudaSuccess) e = configure_r<2>(plan);
+    if (e == cudaSuccess) e = configure_r<4>(plan);
     return e;
 }
 
@@ -246,12 +290,7 @@ P2P_API p2p_status p2p_apply_stage(const p2p_plan* plan, const void* lambda, int
     const bool red = plan->layout == P2P_LAYOUT_REDUNDANT && path != P2P_PATH_TC_BF16X3;
     const int32_t* rows = red ? plan->pk_src : plan->perm;
     const int64_t nrows = red ? plan->packed : plan->n;
-    const int64_t total = nrows * nrhs;
-    if (total > 0) {
-        k_gather_rows<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const float2*)lambda, ld, rows, nrows, nrhs,
-                                                                     plan->lam_buf);
-        P2P_CHECK_LAUNCH("p2p_apply_stage");
-    }
+    P2P_TRY_CUDA(stage_rows((const float2*)lambda, ld, rows, nrows, nrhs, plan->lam_buf, s), "p2p_apply_stage");
     return P2P_OK;
 }
 
@@ -303,12 +342,9 @@ P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, con
     if (plan->n == 0) return P2P_OK;
     if (!grad || ((uintptr_t)grad & 3)) return P2P_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t total = plan->n * nrhs;
-    const unsigned blocks = (unsigned)((total + 255) / 256);
-    k_gather_rows<<<blocks, 256, 0, s>>>((const float2*)lambda, ld, plan->perm, plan->n, nrhs, plan->lam_buf);
-    P2P_CHECK_LAUNCH("p2p_grad_points/stage");
-    k_gather_rows<<<blocks, 256, 0, s>>>((const float2*)g, ld, plan->perm, plan->n, nrhs, plan->g_buf);
-    P2P_CHECK_LAUNCH("p2p_grad_points/stage");
+    P2P_TRY_CUDA(stage_rows((const float2*)lambda, ld, plan->perm, plan->n, nrhs, plan->lam_buf, s),
+                 "p2p_grad_points/stage");
+    P2P_TRY_CUDA(stage_rows((const float2*)g, ld, plan->perm, plan->n, nrhs, plan->g_buf, s), "p2p_grad_points/stage");
     P2P_TRY_CUDA(cudaMemsetAsync(grad, 0, (size_t)plan->n * 3 * sizeof(float), s), "p2p_grad_points/zero");
     PairArgs a = base_args(plan);
     a.grad = grad;

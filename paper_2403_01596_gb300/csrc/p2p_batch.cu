@@ -294,10 +294,14 @@ P2P_API p2p_status p2p_batch_create(p2p_batch** batch, const p2p_plan* const* pl
         }                                 \
     } while (0)
     int ctas_per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = b->R == 1 ? configure<1>(b->warps, b->warp_bytes, &ctas_per_sm)
-                  : b->R == 2 ? configure<2>(b->warps, b->warp_bytes, &ctas_per_sm)
-                              : configure<4>(b->warps, b->warp_bytes, &ctas_per_sm);
-    FAIL(e, "p2p_batch_create/occupancy");
+    // the requested warps per block, halved until one block's shared memory fits
+    for (; b->warps >= 1; b->warps >>= 1) {
+        cudaError_t e = b->R == 1 ? configure<1>(b->warps, b->warp_bytes, &ctas_per_sm)
+                      : b->R == 2 ? configure<2>(b->warps, b->warp_bytes, &ctas_per_sm)
+                                  : configure<4>(b->warps, b->warp_bytes, &ctas_per_sm);
+        FAIL(e, "p2p_batch_create/occupancy");
+        if (ctas_per_sm > 0) break;
+    }
     FAIL(cudaGetDevice(&dev), "p2p_batch_create");
     FAIL(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "p2p_batch_create");
     if (ctas_per_sm < 1) {
