@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(512, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1) k_pair(
     const int warps = blockDim.x >> 5;
     unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(a.chunk, R);
     run_pipeline<R>(ws, a.chunk, lane, a.items, a.n_items, (int64_t)blockIdx.x * warps + warp,
-                    (int64_t)gridDim.x * warps, a.status, [&](const ItemRec&) -> const PairArgs& { return a; });
+                    (int64_t)gridDim.x * warps, a.status, [&](const ItemRec&) -> const PairArgs* { return &a; });
 }
 
 // ------------------------------------------------------ coordinate gradient --

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(512, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1) k_pair_
     const int warps = blockDim.x >> 5;
     unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(chunk_max, R);
     run_pipeline<R>(ws, chunk_max, lane, recs, total, (int64_t)blockIdx.x * warps + warp, (int64_t)gridDim.x * warps,
-                    geoms[0].a.status, [&](const ItemRec& r) -> const PairArgs& { return geoms[r.b].a; });
+                    geoms[0].a.status, [&](const ItemRec& r) -> const PairArgs* { return &geoms[r.b].a; });
 }
 
 // Sort key of every item: larger cost (targets x staged sources) first.

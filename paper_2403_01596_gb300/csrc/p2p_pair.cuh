@@ -36,7 +36,7 @@
 #define P2P_PAIR_UNROLL 2
 #endif
 #ifndef P2P_PAIR_MIN_BLOCKS
-#define P2P_PAIR_MIN_BLOCKS 2
+#define P2P_PAIR_MIN_BLOCKS 1
 #endif
 
 namespace p2p_pair {
@@ -358,7 +358,7 @@ __device__ __forceinline__ ItemRec gather_rec(int32_t v) {
 }
 
 // The per-warp pipeline over the items first, first + stride, ... of `items`
-// (n of them).  `args_of(rec)` gives the PairArgs an item belongs to.  At the
+// (n of them).  `args_of(rec)` points to the PairArgs an item belongs to.  At the
 // top of iteration k the warp holds records k .. k+2 (lane-distributed) and
 // starts loading record k+3; it issues the index copy of item k+2 (indexed
 // layout) and the data copies of item k+1, then waits for item k's data and
@@ -382,8 +382,8 @@ __device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int l
     int32_t v2 = load_rec_lane(items, first + 2 * stride, n, lane);
     ItemRec r0 = gather_rec(v0), r1 = gather_rec(v1);
     const bool has1 = first + stride < n;
-    const PairArgs* a0 = &args_of(r0);
-    const PairArgs* a1 = has1 ? &args_of(r1) : nullptr;
+    const PairArgs* a0 = args_of(r0);
+    const PairArgs* a1 = has1 ? args_of(r1) : nullptr;
     if (lane == 0) {
         if (!a0->red) issue_index_copy(*a0, r0, w, 0);
         if (a1 && !a1->red) issue_index_copy(*a1, r1, w, 1);
@@ -400,7 +400,7 @@ __device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int l
         const int64_t i1 = first + (k + 1) * stride, i2 = first + (k + 2) * stride, i3 = first + (k + 3) * stride;
         const int32_t v3 = load_rec_lane(items, i3, n, lane);  // consumed two iterations later
         const ItemRec r2 = gather_rec(v2);
-        const PairArgs* a2 = i2 < n ? &args_of(r2) : nullptr;
+        const PairArgs* a2 = i2 < n ? args_of(r2) : nullptr;
         // index copy of item k+2 into index stage cur (item k's indices are no longer needed)
         if (a2 && !a2->red && lane == 0) issue_index_copy(*a2, r2, w, cur);
         // data of item k+1
