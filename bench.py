@@ -623,7 +623,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--layout", choices=("auto", "indexed", "redundant"), default="indexed")
+    ap.add_argument("--layout", choices=("auto", "indexed", "redundant", "symmetric"), default="indexed")
     ap.add_argument("--chunk", type=int, default=0, help="sources per work item (0: library default)")
     ap.add_argument("--warps", type=int, default=0, help="warps per block (0: library default)")
     ap.add_argument("--target-group", type=int, default=0, help="targets per sweep (0: library default)")

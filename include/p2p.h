@@ -20,6 +20,13 @@
  *                         neighbourhood (the redundancy of Sec. 3.3, kept per box
  *                         rather than per target), so each thread block reads one
  *                         contiguous tile independent of all others.
+ *   P2P_LAYOUT_SYMMETRIC  the indexed gather over half of each neighbourhood: a box
+ *                         lists its own sources and those of its neighbours with a
+ *                         higher id, and every pair of points in different boxes is
+ *                         evaluated once and added to both ends (G(x, y) = G(y, x)).
+ *                         Same results, about half the kernel evaluations; results
+ *                         are accumulated with atomics.  p2p_grad_points needs an
+ *                         indexed or redundant plan.
  *
  * Conventions shared by every entry point
  *   - Memory.  Pointers marked [dev] are CUDA device pointers, [host] are host
@@ -72,7 +79,7 @@ typedef enum {
 
 typedef enum { P2P_HELMHOLTZ = 0, P2P_LAPLACE = 1 } p2p_kernel;
 
-typedef enum { P2P_LAYOUT_INDEXED = 0, P2P_LAYOUT_REDUNDANT = 1 } p2p_layout;
+typedef enum { P2P_LAYOUT_INDEXED = 0, P2P_LAYOUT_REDUNDANT = 1, P2P_LAYOUT_SYMMETRIC = 2 } p2p_layout;
 
 /* Evaluation path of p2p_apply_path (the plain p2p_apply picks P2P_PATH_AUTO). */
 typedef enum {

@@ -25,6 +25,7 @@ P2P_HELMHOLTZ = 0
 P2P_LAPLACE = 1
 P2P_LAYOUT_INDEXED = 0
 P2P_LAYOUT_REDUNDANT = 1
+P2P_LAYOUT_SYMMETRIC = 2
 P2P_PATH_AUTO = 0
 P2P_PATH_FP32_PER_RHS = 1
 P2P_PATH_FP32_SHARED = 2

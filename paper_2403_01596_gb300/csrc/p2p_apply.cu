@@ -341,6 +341,7 @@ P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, con
     if (st != P2P_OK) return st;
     if (plan->n == 0) return P2P_OK;
     if (!grad || ((uintptr_t)grad & 3)) return P2P_ERR_INVALID;
+    if (plan->layout == P2P_LAYOUT_SYMMETRIC) return P2P_ERR_UNSUPPORTED;  // needs the full source lists
     cudaStream_t s = (cudaStream_t)stream;
     P2P_TRY_CUDA(stage_rows((const float2*)lambda, ld, plan->perm, plan->n, nrhs, plan->lam_buf, s),
                  "p2p_grad_points/stage");

@@ -66,14 +66,17 @@ struct PairArgs {
     int32_t atomic_out;
     int32_t kernel;
     int32_t red;
+    int32_t sym;            // symmetric layout: unordered pairs of different boxes once, added to both ends
 };
 
 // Per-warp shared memory: two data stages (coordinates + R strengths per
-// source), two index stages (the chunk's source list, indexed layout), the
-// slice-reduction buffer and four mbarriers (two for data, two for indices).
+// source), three index stages (the chunk's source list; an item's list stays
+// until its results are scattered), the slice-reduction buffer, the source-side
+// accumulator of the symmetric layout, and five mbarriers (two for data, three
+// for indices).
 __host__ __device__ inline int stage_bytes(int chunk, int R) { return chunk * 16 + chunk * R * 8; }
 __host__ __device__ inline int warp_smem_bytes(int chunk, int R) {
-    return 2 * stage_bytes(chunk, R) + 2 * chunk * 4 + 32 * kMaxTT * R * 8 + 32;
+    return 2 * stage_bytes(chunk, R) + 3 * chunk * 4 + 32 * kMaxTT * R * 8 + chunk * R * 8 + 48;
 }
 
 // ------------------------------------------------------------ async copies --
@@ -128,9 +131,10 @@ struct Stage {
 
 struct WarpSmem {
     unsigned char* data;  // two data stages
-    int* idx;             // two index stages of `chunk` ints
+    int* idx;             // three index stages of `chunk` ints
     float2* red;
-    uint64_t* bar;        // bar[0..1]: data stages, bar[2..3]: index stages
+    float2* src_acc;      // chunk * R source-side sums (symmetric layout)
+    uint64_t* bar;        // bar[0..1]: data stages, bar[2..4]: index stages
     int chunk;
     int R;
     __device__ __forceinline__ Stage stage(int i) const {
@@ -145,9 +149,14 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char* ws, int chunk, int 
     w.chunk = chunk;
     w.R = R;
     w.data = ws;
-    w.idx = reinterpret_cast<int*>(ws + 2 * stage_bytes(chunk, R));
-    w.red = reinterpret_cast<float2*>(ws + 2 * stage_bytes(chunk, R) + 2 * chunk * 4);
-    w.bar = reinterpret_cast<uint64_t*>(ws + 2 * stage_bytes(chunk, R) + 2 * chunk * 4 + 32 * kMaxTT * R * 8);
+    unsigned char* q = ws + 2 * stage_bytes(chunk, R);
+    w.idx = reinterpret_cast<int*>(q);
+    q += 3 * chunk * 4;
+    w.red = reinterpret_cast<float2*>(q);
+    q += 32 * kMaxTT * R * 8;
+    w.src_acc = reinterpret_cast<float2*>(q);
+    q += chunk * R * 8;
+    w.bar = reinterpret_cast<uint64_t*>(q);
     return w;
 }
 
@@ -163,9 +172,10 @@ __device__ __forceinline__ void issue_index_copy(const PairArgs& a, const ItemRe
 // One item ahead: the chunk's coordinates and (when one pass covers every
 // right-hand side, nrhs == R) strengths into data stage `i`.  Redundant: two
 // TMA bulk copies of the contiguous tile (lane 0).  Indexed: per-lane cp.async
-// gathers through the index stage `i`, which the caller has waited for.
+// gathers through index stage `ii`, which the caller has waited for.
 template <int R>
-__device__ __forceinline__ void issue_data(const PairArgs& a, const ItemRec& r, const WarpSmem& w, int i, int lane) {
+__device__ __forceinline__ void issue_data(const PairArgs& a, const ItemRec& r, const WarpSmem& w, int i, int ii,
+                                           int lane) {
     const Stage st = w.stage(i);
     const bool lam_async = a.nrhs == R;
     if (a.red) {
@@ -179,7 +189,7 @@ __device__ __forceinline__ void issue_data(const PairArgs& a, const ItemRec& r, 
             if (lam_async) bulk_g2s(st.sl, a.lam + (int64_t)r.src_off * R, n4 * (uint32_t)R * 8u, &w.bar[i]);
         }
     } else {
-        const int* idx = w.index(i);
+        const int* idx = w.index(ii);
         for (int p = lane; p < r.ns; p += 32) {
             const int j = idx[p];
             cp_async16(st.sx + p, a.xs + j);
@@ -310,6 +320,153 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
     __syncwarp();
 }
 
+// Symmetric layout: sources of the own box (the chunk's first m_end) are swept
+// as in the plain layout; every other source s meets the lane's TT targets
+// once, adding G lambda_s to the targets and G lambda_t to s.  The source-side
+// partials of the G lanes that share a slice are summed with a segmented
+// shuffle reduction and lane g = 0 adds them to src_acc[s].  Rounds over the
+// chunk run the same number of times in every lane so the shuffles converge.
+template <int KERN, int R, int TT>
+__device__ __forceinline__ void sweep_targets_sym(const PairArgs& a, const float4* __restrict__ sx,
+                                                  const float2* __restrict__ sl, float2* red, float2* src_acc, int ns,
+                                                  int m_end, int tbase, int nt, int32_t map, int rb, int lane) {
+    const int G = map_g(map), Q = map_q(map);
+    const int q = map_div(map, lane);
+    const int g = lane - q * G;
+    float4 tx[TT];
+    float2 tl[TT][R];
+    float2 acc[TT][R];
+#pragma unroll
+    for (int u = 0; u < TT; ++u) {
+        const int t = g + u * G;
+        const bool ok = t < nt && q < Q;
+        tx[u] = ok ? a.xs[tbase + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            tl[u][r] = (ok && rb + r < a.nrhs) ? a.lam[(int64_t)(tbase + t) * a.nrhs + rb + r] : make_float2(0.f, 0.f);
+            acc[u][r] = make_float2(0.f, 0.f);
+        }
+    }
+    const float k = a.k;
+    if (q < Q) {
+        for (int s = q; s < m_end; s += Q) pair_step<KERN, R, TT, true>(sx, sl, s, tx, acc, k);
+    }
+    const int m0 = m_end / Q, m1 = (ns + Q - 1) / Q;
+    for (int m = m0; m < m1; ++m) {
+        const int s = m * Q + q;
+        const bool active = q < Q && s >= m_end && s < ns;
+        float2 ps[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) ps[r] = make_float2(0.f, 0.f);
+        if (active) {
+            const float4 p = sx[s];
+            float2 l[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) l[r] = sl[s * R + r];
+#pragma unroll
+            for (int u = 0; u < TT; ++u) {
+                const float dx = p.x - tx[u].x, dy = p.y - tx[u].y, dz = p.z - tx[u].z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float inv = rsqrtf(fmaxf(r2, 1.17549435e-38f));
+                float gr = inv, gi = 0.f;
+                if (KERN == P2P_HELMHOLTZ) {
+                    float sn, cs;
+                    __sincosf(k * (r2 * inv), &sn, &cs);
+                    gr = cs * inv;
+                    gi = sn * inv;
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    acc[u][r].x = fmaf(gr, l[r].x, fmaf(-gi, l[r].y, acc[u][r].x));
+                    acc[u][r].y = fmaf(gr, l[r].y, fmaf(gi, l[r].x, acc[u][r].y));
+                    ps[r].x = fmaf(gr, tl[u][r].x, fmaf(-gi, tl[u][r].y, ps[r].x));
+                    ps[r].y = fmaf(gr, tl[u][r].y, fmaf(gi, tl[u][r].x, ps[r].y));
+                }
+            }
+        }
+        for (int off = 1; off < G; off <<= 1) {
+            const bool take = g + off < G;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float x = __shfl_down_sync(P2P_FULL_MASK, ps[r].x, off);
+                const float y = __shfl_down_sync(P2P_FULL_MASK, ps[r].y, off);
+                if (take) {
+                    ps[r].x += x;
+                    ps[r].y += y;
+                }
+            }
+        }
+        if (active && g == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 v = src_acc[s * R + r];
+                v.x += ps[r].x;
+                v.y += ps[r].y;
+                src_acc[s * R + r] = v;
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < TT; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) red[(u * 32 + lane) * R + r] = acc[u][r];
+    __syncwarp();
+    for (int t = lane; t < nt; t += 32) {
+        const int u = map_div(map, t);
+        const int gg = t - u * G;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = make_float2(0.f, 0.f);
+        for (int qq = 0; qq < Q; ++qq) {
+            const int l2 = qq * G + gg;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 w = red[(u * 32 + l2) * R + r];
+                v[r].x += w.x;
+                v[r].y += w.y;
+            }
+        }
+        const int64_t row = (int64_t)a.perm[tbase + t] * a.ld + rb;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (rb + r < a.nrhs) atomicAdd(a.out + row + r, make_float2(v[r].x * kInv4Pi, v[r].y * kInv4Pi));
+    }
+    __syncwarp();
+}
+
+template <int KERN, int R>
+__device__ __forceinline__ void compute_item_sym(const PairArgs& a, const ItemRec& r, const Stage& st, const int* idx,
+                                                 float2* red, float2* src_acc, int lane) {
+    for (int rb = 0; rb < a.nrhs; rb += R) {
+        if (a.nrhs != R) {
+            __syncwarp();
+            load_lam_block<R>(a, r, st.sl, rb, lane);
+        }
+        for (int p = lane; p < r.ns * R; p += 32) src_acc[p] = make_float2(0.f, 0.f);
+        __syncwarp();
+        for (int t0 = 0; t0 < r.nt; t0 += a.tg) {
+            const int nt = min(a.tg, r.nt - t0);
+            const int32_t map = (t0 + a.tg >= r.nt) ? r.map_last : r.map_full;
+            const int tt = map_tt(map);
+            if (tt == 1) sweep_targets_sym<KERN, R, 1>(a, st.sx, st.sl, red, src_acc, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
+            else if (tt == 2) sweep_targets_sym<KERN, R, 2>(a, st.sx, st.sl, red, src_acc, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
+            else sweep_targets_sym<KERN, R, 4>(a, st.sx, st.sl, red, src_acc, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
+        }
+        // scatter the source-side sums of the sources outside the own box
+        for (int p = r.m_end + lane; p < r.ns; p += 32) {
+            const int64_t row = (int64_t)a.perm[idx[p]] * a.ld + rb;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                if (rb + q < a.nrhs) {
+                    const float2 v = src_acc[p * R + q];
+                    atomicAdd(a.out + row + q, make_float2(v.x * kInv4Pi, v.y * kInv4Pi));
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Sweeps every target group of item `r` against its staged chunk, for every
 // block of R right-hand sides.
 template <int KERN, int R>
@@ -333,10 +490,15 @@ __device__ __forceinline__ void compute_item(const PairArgs& a, const ItemRec& r
 }
 
 template <int R>
-__device__ __forceinline__ void compute_dispatch(const PairArgs& a, const ItemRec& r, const Stage& st, float2* red,
-                                                 int lane) {
-    if (a.kernel == P2P_HELMHOLTZ) compute_item<P2P_HELMHOLTZ, R>(a, r, st, red, lane);
-    else compute_item<P2P_LAPLACE, R>(a, r, st, red, lane);
+__device__ __forceinline__ void compute_dispatch(const PairArgs& a, const ItemRec& r, const Stage& st, const int* idx,
+                                                 float2* red, float2* src_acc, int lane) {
+    if (a.sym) {
+        if (a.kernel == P2P_HELMHOLTZ) compute_item_sym<P2P_HELMHOLTZ, R>(a, r, st, idx, red, src_acc, lane);
+        else compute_item_sym<P2P_LAPLACE, R>(a, r, st, idx, red, src_acc, lane);
+    } else {
+        if (a.kernel == P2P_HELMHOLTZ) compute_item<P2P_HELMHOLTZ, R>(a, r, st, red, lane);
+        else compute_item<P2P_LAPLACE, R>(a, r, st, red, lane);
+    }
 }
 
 // Item record distributed over lanes 0..7 of a warp (field f in lane f).
@@ -360,21 +522,22 @@ __device__ __forceinline__ ItemRec gather_rec(int32_t v) {
 // The per-warp pipeline over the items first, first + stride, ... of `items`
 // (n of them).  `args_of(rec)` points to the PairArgs an item belongs to.  At the
 // top of iteration k the warp holds records k .. k+2 (lane-distributed) and
-// starts loading record k+3; it issues the index copy of item k+2 (indexed
-// layout) and the data copies of item k+1, then waits for item k's data and
-// sweeps it.  Every mbarrier wait is bounded.
+// starts loading record k+3; it issues the index copy of item k+2 (index stage
+// (k+2) % 3, indexed layouts) and the data copies of item k+1 (data stage
+// (k+1) % 2), then waits for item k's data and sweeps it.  Every mbarrier wait
+// is bounded.
 template <int R, typename ArgsOf>
 __device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int lane, const ItemRec* items, int64_t n,
                                              int64_t first, int64_t stride, unsigned int* status, ArgsOf args_of) {
     const WarpSmem w = warp_smem(ws, chunk, R);
     if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&w.bar[i]);
+        for (int i = 0; i < 5; ++i) mbar_init(&w.bar[i]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
     if (first >= n) return;
-    uint32_t parity[4] = {0u, 0u, 0u, 0u};
+    uint32_t parity[5] = {0u, 0u, 0u, 0u, 0u};
     bool failed = false;
     // prologue: records 0..2, index copies of items 0 and 1, data of item 0
     int32_t v0 = load_rec_lane(items, first, n, lane);
@@ -393,25 +556,26 @@ __device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int l
         parity[2] ^= 1u;
     }
     failed = !__all_sync(P2P_FULL_MASK, !failed);
-    if (!failed) issue_data<R>(*a0, r0, w, 0, lane);
+    if (!failed) issue_data<R>(*a0, r0, w, 0, 0, lane);
     int64_t k = 0;
     while (!failed) {
         const int cur = (int)(k & 1), nxt = cur ^ 1;
+        const int i0 = (int)(k % 3), i1s = (int)((k + 1) % 3), i2s = (int)((k + 2) % 3);  // index stages
         const int64_t i1 = first + (k + 1) * stride, i2 = first + (k + 2) * stride, i3 = first + (k + 3) * stride;
         const int32_t v3 = load_rec_lane(items, i3, n, lane);  // consumed two iterations later
         const ItemRec r2 = gather_rec(v2);
         const PairArgs* a2 = i2 < n ? args_of(r2) : nullptr;
-        // index copy of item k+2 into index stage cur (item k's indices are no longer needed)
-        if (a2 && !a2->red && lane == 0) issue_index_copy(*a2, r2, w, cur);
+        // index copy of item k+2 (item k's list stays in its own stage until it is scattered)
+        if (a2 && !a2->red && lane == 0) issue_index_copy(*a2, r2, w, i2s);
         // data of item k+1
         if (a1) {
             if (!a1->red) {
-                failed |= !mbar_wait(&w.bar[2 + nxt], parity[2 + nxt]);
-                parity[2 + nxt] ^= 1u;
+                failed |= !mbar_wait(&w.bar[2 + i1s], parity[2 + i1s]);
+                parity[2 + i1s] ^= 1u;
                 failed = !__all_sync(P2P_FULL_MASK, !failed);
                 if (failed) break;
             }
-            issue_data<R>(*a1, r1, w, nxt, lane);
+            issue_data<R>(*a1, r1, w, nxt, i1s, lane);
         }
         // wait for item k's data
         if (a0->red) {
@@ -423,7 +587,7 @@ __device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int l
         __syncwarp();
         failed = !__all_sync(P2P_FULL_MASK, !failed);
         if (failed) break;
-        compute_dispatch<R>(*a0, r0, w.stage(cur), w.red, lane);
+        compute_dispatch<R>(*a0, r0, w.stage(cur), w.index(i0), w.red, w.src_acc, lane);
         __syncwarp();
         if (!a1) break;
         r0 = r1;
@@ -437,7 +601,7 @@ __device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int l
     if (failed) {
         if (lane == 0) atomicOr(status, P2P_DEV_TIMEOUT);
         // drain every bulk copy that may still be in flight (bounded), then the cp.async groups
-        for (int i = 0; i < 4; ++i) mbar_wait(&w.bar[i], parity[i], 1u << 20);
+        for (int i = 0; i < 5; ++i) mbar_wait(&w.bar[i], parity[i], 1u << 20);
         cp_async_wait<0>();
         __syncwarp();
     }
@@ -464,6 +628,8 @@ inline PairArgs base_args(const p2p_plan* p) {
     a.atomic_out = p->max_chunks > 1;
     a.kernel = p->kernel;
     a.red = p->layout == P2P_LAYOUT_REDUNDANT;
+    a.sym = p->layout == P2P_LAYOUT_SYMMETRIC;
+    if (a.sym) a.atomic_out = 1;  // sources scatter into other boxes' targets
     return a;
 }
 

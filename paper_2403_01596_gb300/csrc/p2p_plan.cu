@@ -160,13 +160,13 @@ __global__ void k_gather_xyz(const float* __restrict__ pts, const int32_t* __res
 // Per box: S_b, work-item count ceil(S_b / chunk) and the padded length of its
 // source list.  Validates the CSR (ascending ids in range, own box present).
 __global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ nbr_ptr,
-                           const int32_t* __restrict__ nbr_idx, int32_t nb, int64_t nnz, int chunk,
-                           int32_t* __restrict__ box_src, int32_t* __restrict__ n_chunks, int32_t* __restrict__ padded, int32_t* __restrict__ maxes,
+                           const int32_t* __restrict__ nbr_idx, int32_t nb, int64_t nnz, int chunk, int upper,
+                           int32_t* __restrict__ box_src, int32_t* __restrict__ list_len, int32_t* __restrict__ n_chunks, int32_t* __restrict__ padded, int32_t* __restrict__ maxes,
                            unsigned int* __restrict__ status) {
     int32_t b = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (b >= nb) return;
     int32_t e0 = nbr_ptr[b], e1 = nbr_ptr[b + 1];
-    int64_t s = 0, self = -1;
+    int64_t s = 0, self = -1, s_up = 0;
     bool ok = e0 >= 0 && e1 >= e0 && e1 <= nnz && e1 - e0 <= 27;
     if (ok) {
         for (int32_t e = e0; e < e1; ++e) {
@@ -177,18 +177,22 @@ __global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* _
             }
             if (c == b) self = s;
             s += box_ptr[c + 1] - box_ptr[c];
+            if (c >= b) s_up += box_ptr[c + 1] - box_ptr[c];
         }
     }
     int32_t own = box_ptr[b + 1] - box_ptr[b];
     if (!ok || self < 0 || own <= 0 || s > INT32_MAX - 4) {
         atomicOr(status, P2P_DEV_BAD_INPUT);
         s = 0;
+        s_up = 0;
         self = 0;
     }
     box_src[b] = (int32_t)s;
-    int32_t c = (int32_t)((s + chunk - 1) / chunk);
+    const int64_t len = upper ? s_up : s;  // length of the box's source list
+    list_len[b] = (int32_t)len;
+    int32_t c = (int32_t)((len + chunk - 1) / chunk);
     n_chunks[b] = c;
-    padded[b] = (int32_t)((s + 3) & ~3ll);
+    padded[b] = (int32_t)((len + 3) & ~3ll);
     atomicMax(&maxes[0], c);
     atomicMax(&maxes[1], own);
 }
@@ -196,13 +200,13 @@ __global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* _
 // Work-item records (unsorted) and their sort keys: larger cost (targets x
 // sources) first.
 __global__ void k_item_records(const int32_t* __restrict__ n_chunks, const int32_t* __restrict__ item_off,
-                               const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ box_src,
+                               const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ list_len,
                                const int32_t* __restrict__ pk_off, int32_t nb, int chunk, int tg,
                                ItemRec* __restrict__ recs, uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
     int32_t b = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (b >= nb) return;
     const int32_t c = n_chunks[b], o = item_off[b];
-    const int32_t tb = box_ptr[b], nt = box_ptr[b + 1] - tb, S = box_src[b];
+    const int32_t tb = box_ptr[b], nt = box_ptr[b + 1] - tb, S = list_len[b];
     const int32_t last = nt - ((nt - 1) / tg) * tg;  // targets of the last target group
     for (int32_t i = 0; i < c; ++i) {
         const int32_t s0 = i * chunk;
@@ -234,16 +238,23 @@ __global__ void k_item_gather(const ItemRec* __restrict__ recs, const int32_t* _
 // copy of the coordinates plus original indices (the repetition of Sec. 3.3).
 __global__ void k_pack(const float4* __restrict__ xs, const int32_t* __restrict__ perm,
                        const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ nbr_ptr,
-                       const int32_t* __restrict__ nbr_idx, const int32_t* __restrict__ pk_off, int32_t nb,
+                       const int32_t* __restrict__ nbr_idx, const int32_t* __restrict__ pk_off, int32_t nb, int upper,
                        int32_t* __restrict__ nb_src, float4* __restrict__ pk_xyz, int32_t* __restrict__ pk_src) {
     const int lane = threadIdx.x & 31;
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
-    const int32_t e0 = nbr_ptr[b], ne = nbr_ptr[b + 1] - e0;
+    const int32_t e0 = nbr_ptr[b];
+    int32_t ne = nbr_ptr[b + 1] - e0;
     const int32_t c = lane < ne ? nbr_idx[e0 + lane] : -1;
     const unsigned selfm = __ballot_sync(P2P_FULL_MASK, c == (int32_t)b);
     const int sp = selfm ? __ffs(selfm) - 1 : 0;
-    const int from = lane == 0 ? sp : (lane <= sp ? lane - 1 : lane);
+    // full list: slot 0 <- own box, slots 1..sp <- entries 0..sp-1, later slots unchanged;
+    // upper list (own box and higher ids only): slot i <- entry sp + i
+    int from = lane == 0 ? sp : (lane <= sp ? lane - 1 : lane);
+    if (upper) {
+        from = min(sp + lane, 31);
+        ne -= sp;
+    }
     const int32_t cs = __shfl_sync(P2P_FULL_MASK, c, from);
     int32_t start = 0, len = 0;
     if (lane < ne) {
@@ -376,7 +387,7 @@ p2p_tuning resolve_tuning(const p2p_tuning* t) {
 
 struct PlanLayout {
     p2p_plan p;  // pointers only
-    int32_t *n_chunks, *item_off, *padded, *maxes, *small;
+    int32_t *n_chunks, *item_off, *padded, *maxes, *small, *list_len;
     void* scan_ws;
     // item-sort scratch (aliases the strength staging buffer when it is large enough)
     ItemRec* recs;
@@ -410,6 +421,7 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, p2p_layout layout
     L.p.lam_buf = c.take<float2>(lam_rows * (size_t)max_nrhs);
     L.p.g_buf = c.take<float2>(m * (size_t)max_nrhs);
     L.n_chunks = c.take<int32_t>(mb);
+    L.list_len = c.take<int32_t>(mb);
     L.item_off = c.take<int32_t>(mb + 1);
     L.padded = c.take<int32_t>(mb);
     L.maxes = c.take<int32_t>(4);
@@ -558,7 +570,7 @@ P2P_API p2p_status p2p_plan_workspace_size(int64_t n, int32_t num_boxes, int64_t
     (void)nnz;
     if (!bytes || n < 0 || n >= INT32_MAX || num_boxes < 0 || num_boxes > n || sources < 0 ||
         sources >= INT32_MAX || max_nrhs < 1 || max_nrhs > 256 ||
-        (layout != P2P_LAYOUT_INDEXED && layout != P2P_LAYOUT_REDUNDANT))
+        (layout != P2P_LAYOUT_INDEXED && layout != P2P_LAYOUT_REDUNDANT && layout != P2P_LAYOUT_SYMMETRIC))
         return P2P_ERR_INVALID;
     p2p_tuning t = resolve_tuning(tuning);
     if (!tuning_valid(t)) return P2P_ERR_INVALID;
@@ -625,17 +637,18 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
     FAIL_CUDA(cudaMemsetAsync(L.maxes, 0, 4 * sizeof(int32_t), s), "p2p_plan_create");
     k_gather_xyz<<<blocks_for(n, kThreads), kThreads, 0, s>>>(pts, perm, n, p->xs);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/gather");
+    const int upper = layout == P2P_LAYOUT_SYMMETRIC;
     k_box_info<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(box_ptr, nbr_ptr, nbr_idx, num_boxes, nnz,
-                                                                     t.chunk, p->box_src, L.n_chunks, L.padded,
-                                                                     L.maxes, p->status);
+                                                                     t.chunk, upper, p->box_src, L.list_len,
+                                                                     L.n_chunks, L.padded, L.maxes, p->status);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/box_info");
     FAIL_CUDA(scan_exclusive_i32(L.n_chunks, L.item_off, num_boxes, L.small, L.scan_ws, s), "p2p_plan_create/scan");
     FAIL_CUDA(scan_exclusive_i32(L.padded, p->pk_off, num_boxes, p->pk_off + num_boxes, L.scan_ws, s),
               "p2p_plan_create/scan_lists");
     k_pack<<<blocks_for((int64_t)num_boxes * 32, kThreads), kThreads, 0, s>>>(
-        p->xs, perm, box_ptr, nbr_ptr, nbr_idx, p->pk_off, num_boxes, p->nb_src, p->pk_xyz, p->pk_src);
+        p->xs, perm, box_ptr, nbr_ptr, nbr_idx, p->pk_off, num_boxes, upper, p->nb_src, p->pk_xyz, p->pk_src);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/pack");
-    k_item_records<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(L.n_chunks, L.item_off, box_ptr, p->box_src,
+    k_item_records<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(L.n_chunks, L.item_off, box_ptr, L.list_len,
                                                                         p->pk_off, num_boxes, t.chunk, t.target_group,
                                                                         L.recs, L.keys, L.vals);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/items");

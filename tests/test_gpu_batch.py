@@ -41,6 +41,9 @@ def _geometries(api, nrhs):
     u = W.uniform_cube(8192, 63)
     geo.append(dict(points=u, lo=(0, 0, 0), h=0.25, ng=4, k=0.0, kernel="laplace", layout="indexed",
                     tuning={"chunk": 64, "warps_per_cta": 4}))
+    e = W.ellipsoid_211(12000, 64)
+    geo.append(dict(points=e, lo=(-2, -2, -2), h=4 / 40, ng=40, k=12.0, kernel="helmholtz", layout="symmetric",
+                    tuning=None))
     plans = []
     for g in geo:
         plans.append(api.Plan(torch.from_numpy(g["points"]).cuda(), g["lo"], g["h"], g["ng"], g["k"],

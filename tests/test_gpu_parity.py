@@ -75,7 +75,7 @@ def test_binning_and_neighbors_bit_exact(case):
 
 
 @pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
-@pytest.mark.parametrize("layout", ["indexed", "redundant"])
+@pytest.mark.parametrize("layout", ["indexed", "redundant", "symmetric"])
 def test_apply_dense_cube(kernel, layout):
     """Uniform cube, 8^3 boxes (~64 points per box, ~1350 sources per box: several chunks)."""
     api = _cuda()
@@ -91,7 +91,7 @@ def test_apply_dense_cube(kernel, layout):
     assert plan.pair_count() == oracle.pair_count(wl.points, wl.lo, wl.h, wl.ng)
 
 
-@pytest.mark.parametrize("layout", ["indexed", "redundant"])
+@pytest.mark.parametrize("layout", ["indexed", "redundant", "symmetric"])
 @pytest.mark.parametrize("case", ["sphere40", "clustered", "ellipsoid"])
 def test_apply_surfaces(layout, case):
     api = _cuda()
@@ -112,7 +112,7 @@ def test_apply_tunings(tuning):
     wl = _clustered(12000, 13)
     lam = W.strengths(wl.n, 1, 3)
     ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
-    for layout in ("indexed", "redundant"):
+    for layout in ("indexed", "redundant", "symmetric"):
         plan = _plan(api, wl, "helmholtz", layout, tuning=tuning)
         out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
         assert rel_l2(out, ref).max() <= TOL, (layout, tuning)
@@ -125,7 +125,7 @@ def test_multi_rhs(path, nrhs):
     wl = _small_sphere(20000, 30, 8)
     lam = W.strengths(wl.n, nrhs, 8)
     ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
-    for layout in ("indexed", "redundant"):
+    for layout in ("indexed", "redundant", "symmetric"):
         plan = _plan(api, wl, "helmholtz", layout, max_nrhs=nrhs)
         out = plan.apply(torch.from_numpy(lam).cuda(), path=path).cpu().numpy()
         err = rel_l2(out, ref)
@@ -136,7 +136,7 @@ def test_adjoint():
     api = _cuda()
     wl = _small_sphere(30000, 36, 9)
     g = W.strengths(wl.n, 2, 9)
-    for layout in ("indexed", "redundant"):
+    for layout in ("indexed", "redundant", "symmetric"):
         plan = _plan(api, wl, "helmholtz", layout, max_nrhs=2)
         out = plan.apply(torch.from_numpy(g).cuda(), adjoint=True).cpu().numpy()
         ref = oracle.p2p(wl.points, g, wl.lo, wl.h, wl.ng, wl.k, adjoint=True)
@@ -196,8 +196,8 @@ def test_edge_cases():
     wl = W.Workload("edge", p, (0, 0, 0), 0.125, 8, 9.0, 0)
     lam = W.strengths(len(p), 1, 4)
     ref = oracle.p2p(p, lam, wl.lo, wl.h, wl.ng, wl.k)
-    for layout in ("indexed", "redundant"):
-        for tuning in (None, {"chunk": 32, "target_group": 32}):
+    for layout in ("indexed", "redundant", "symmetric"):
+        for tuning in (None, {"chunk": 32, "target_group": 32}, {"chunk": 256, "target_group": 128}):
             plan = _plan(api, wl, "helmholtz", layout, tuning=tuning)
             out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
             assert rel_l2(out, ref).max() <= TOL
@@ -227,9 +227,19 @@ def test_full_size_sphere_sampled(occ):
     ref_bins = oracle.bin_points(wl.points, wl.lo, wl.h, wl.ng)
     targets = np.random.default_rng(occ).choice(wl.n, 3000, replace=False)
     ref = oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, wl.k)
-    for layout in ("indexed", "redundant"):
+    for layout in ("indexed", "redundant", "symmetric"):
         plan = _plan(api, wl, "helmholtz", layout)
         assert plan.num_boxes == ref_bins["num_boxes"]
         np.testing.assert_array_equal(plan.structure.perm.cpu().numpy(), ref_bins["perm"])
         out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
         assert rel_l2(out[targets], ref).max() <= TOL
+
+
+def test_symmetric_plan_refuses_gradients():
+    api = _cuda()
+    from paper_2403_01596_gb300._capi import P2PError
+    wl = _small_sphere(3000, 12, 21)
+    plan = _plan(api, wl, "helmholtz", "symmetric")
+    lam = torch.from_numpy(W.strengths(wl.n, 1, 21)).cuda()
+    with pytest.raises(P2PError):
+        plan.grad_points(lam, lam)
