@@ -20,12 +20,14 @@ import statistics
 import threading
 
 DEFAULT_CANDIDATES = (
-    {"chunk": 64, "warps_per_cta": 8, "target_group": 128},
-    {"chunk": 128, "warps_per_cta": 8, "target_group": 128},
-    {"chunk": 128, "warps_per_cta": 4, "target_group": 128},
-    {"chunk": 256, "warps_per_cta": 8, "target_group": 128},
-    {"chunk": 128, "warps_per_cta": 16, "target_group": 128},
+    {"chunk": 128, "warps_per_cta": 8, "target_group": 32},
+    {"chunk": 128, "warps_per_cta": 4, "target_group": 32},
+    {"chunk": 64, "warps_per_cta": 8, "target_group": 32},
+    {"chunk": 256, "warps_per_cta": 4, "target_group": 32},
+    {"chunk": 128, "warps_per_cta": 8, "target_group": 64},
 )
+
+DEFAULT_LAYOUTS = ("indexed", "redundant", "symmetric")
 
 _lock = threading.Lock()
 
@@ -91,7 +93,7 @@ def _time_plan(plan, lam, out, reps: int) -> float:
     return statistics.median(ms)
 
 
-def tune(structure, k: float, kernel: str = "helmholtz", nrhs: int = 1, layouts=("indexed", "redundant"),
+def tune(structure, k: float, kernel: str = "helmholtz", nrhs: int = 1, layouts=DEFAULT_LAYOUTS,
          candidates=DEFAULT_CANDIDATES, reps: int = 7, use_cache: bool = True, path: str | None = None) -> dict:
     """Times every (layout, candidate) on `structure` and returns the best as
     {"layout", "tuning", "ms", "key", "cached"}."""
