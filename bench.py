@@ -574,7 +574,8 @@ def run_batched(args):
     for g in range(len(W.BATCH_SIZES)):
         geo = W.batch_geometry(g, args.scale)
         pts = torch.from_numpy(geo["points"]).cuda()
-        st = api.choose_grid_ct(pts, geo["lo"], geo["extent"], 128, ng_start=16)
+        st = api.BoxStructure(pts, geo["lo"], geo["h"], geo["ng"])
+        st.max_occupancy = int((st.box_ptr[1:] - st.box_ptr[:-1]).max().item())
         k = 2 * np.pi * geo["edge_wavelengths"] / st.h
         plan = api.Plan(pts, geo["lo"], st.h, st.ng, k, max_nrhs=nrhs, structure=st)
         plans.append(plan)

@@ -83,7 +83,7 @@ def cylinder_plates(n: int, seed: int, sigma: float = 0.02, clusters: int = 64) 
 
     Half the points are uniform by area; the other half come from `clusters`
     Gaussian clusters (std `sigma` in arc-length / plate coordinates) whose
-    centres are uniform by area.  This gives box occupancies from 1 to ~100+.
+    centres are uniform by area.
     """
     rng = np.random.default_rng(seed)
     a_cyl, a_plate = 2.0 * math.pi * 0.5 * 2.0, 4.0
@@ -112,16 +112,25 @@ def cylinder_plates(n: int, seed: int, sigma: float = 0.02, clusters: int = 64) 
     n_uni = n // 2
     n_clu = n - n_uni
     part_u, s_u, t_u = surface_params(n_uni)
-    cpart, cs, ct = surface_params(clusters)
-    which = rng.integers(0, clusters, size=n_clu)
+    cpart, cs, ct = surface_params(max(1, clusters))
+    which = rng.integers(0, max(1, clusters), size=n_clu)
     part_c = cpart[which]
     s_c = cs[which] + sigma * rng.standard_normal(n_clu)
     t_c = ct[which] + sigma * rng.standard_normal(n_clu)
-    # the cylinder's arc-length coordinate wraps around its circumference
-    s_c = np.where(part_c == 0, np.mod(s_c, TWO_PI * 0.5), s_c)
+    # the cylinder's arc-length coordinate wraps around its circumference; coordinates that leave
+    # [-1, 1] (plate sides, cylinder height) are mirrored back so no edge collects points
+    def mirror(x):
+        y = np.mod(x + 1.0, 4.0)
+        return 1.0 - np.abs(y - 2.0)
+    s_c = np.where(part_c == 0, np.mod(s_c, TWO_PI * 0.5), mirror(s_c))
+    t_c = mirror(t_c)
     pts = np.concatenate([embed(part_u, s_u, t_u), embed(part_c, s_c, t_c)])
     pts = pts[rng.permutation(n)]
     return _to_f32(pts)
+
+
+#: area of the cylinder-plus-plates surface
+CYLINDER_PLATES_AREA = 2.0 * math.pi * 0.5 * 2.0 + 2 * 4.0
 
 
 def strengths(n: int, nrhs: int, seed: int) -> np.ndarray:
@@ -173,11 +182,19 @@ BATCH_SIZES = (500_000, 1_000_000, 2_000_000, 3_000_000, 4_000_000, 6_000_000, 7
 
 
 def batch_geometry(g: int, scale: float = 1.0) -> dict:
-    """Geometry g of the batched workload: points, the box (lo, extent) and leaf edge in wavelengths.
+    """Geometry g of the batched workload: points, leaf grid and leaf edge in wavelengths.
 
-    The leaf grid is chosen by the caller (clustering threshold 128 points per
-    box); the wavenumber follows from the chosen h as k = 2 pi * edge / h.
+    The leaf edge h is chosen so that the uniform half of the points fills the
+    surface boxes at about 6 points per box (a surface box holds ~h^2 of area);
+    the clustered half comes in clusters of ~2000 points with std 2h, whose peak
+    occupancy is ~2000 / (8 pi) + 6, about 90 points per box.  Box occupancy
+    therefore spans 1 to ~128.  The grid covers [-1.3, 1.3]^3; the wavenumber
+    follows from h as k = 2 pi * edge / h.
     """
     n = max(1, int(round(BATCH_SIZES[g] * scale)))
-    return {"points": cylinder_plates(n, 10 + g), "lo": (-1.3, -1.3, -1.3), "extent": 2.6,
-            "edge_wavelengths": 0.1 + 0.2 * g / 7.0, "seed": 10 + g, "nrhs": 8}
+    h = math.sqrt(CYLINDER_PLATES_AREA * 6.0 / max(n // 2, 1))
+    ng = max(1, int(math.ceil(2.6 / h)))
+    h = 2.6 / ng
+    clusters = max(1, (n - n // 2) // 2000)
+    return {"points": cylinder_plates(n, 10 + g, sigma=2.0 * h, clusters=clusters), "lo": (-1.3, -1.3, -1.3),
+            "extent": 2.6, "h": h, "ng": ng, "edge_wavelengths": 0.1 + 0.2 * g / 7.0, "seed": 10 + g, "nrhs": 8}
