@@ -3,11 +3,11 @@
 // One batched apply is two kernel launches, both safe to capture in a CUDA
 // graph (no allocation, no host synchronisation, every pointer passed by
 // value):
-//   k_batch_stage   writes each geometry's output pointer into the device
-//                   geometry table, gathers every geometry's strengths into its
-//                   plan's staging buffer (sorted or packed rows), zeroes the
-//                   outputs that are accumulated with atomics and resets the
-//                   work-queue counter;
+//   k_batch_stage   one block row per geometry: writes the geometry's output
+//                   pointer into the device geometry table, gathers its
+//                   strengths into its plan's staging buffer (sorted or packed
+//                   rows) and zeroes its outputs when they are accumulated with
+//                   atomics;
 //   k_pair_batched  a persistent grid (resident blocks x SMs) whose warps take
 //                   work items (geometry, box, source chunk) from one combined
 //                   list ordered by decreasing item cost (targets x sources),
@@ -57,32 +57,34 @@ __device__ __forceinline__ int find_geom(const int64_t* off, int count, int64_t 
     return g;
 }
 
-__global__ void k_batch_stage(BatchGeom* __restrict__ geoms, const BatchIO io, unsigned long long* __restrict__ counter) {
+// Block row blockIdx.y stages geometry blockIdx.y: its output pointer into the
+// geometry table, its strengths into the plan's staging buffer, and zeros for
+// its outputs when they are accumulated with atomics.
+__global__ void k_batch_stage(BatchGeom* __restrict__ geoms, const BatchIO io) {
+    const int g = blockIdx.y;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        geoms[g].a.out = io.out[g];
+        geoms[g].a.ld = io.ld;
+        geoms[g].a.nrhs = io.nrhs;
+    }
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (tid < io.count) {
-        geoms[tid].a.out = io.out[tid];
-        geoms[tid].a.ld = io.ld;
-        geoms[tid].a.nrhs = io.nrhs;
+    const int32_t* __restrict__ rows = geoms[g].rows;
+    float2* __restrict__ dst = const_cast<float2*>(geoms[g].a.lam);
+    const float2* __restrict__ src = io.lam[g];
+    const int64_t n_el = io.row_off[g + 1] - io.row_off[g];
+    for (int64_t i = tid; i < n_el; i += stride) {
+        const int64_t s = i / io.nrhs;
+        const int q = (int)(i - s * io.nrhs);
+        const int32_t r = rows[s];
+        dst[i] = r >= 0 ? src[(int64_t)r * io.ld + q] : make_float2(0.f, 0.f);
     }
-    if (tid == 0) *counter = 0ull;
-    const int64_t rows_total = io.row_off[io.count];
-    for (int64_t i = tid; i < rows_total; i += stride) {
-        const int g = find_geom(io.row_off, io.count, i);
-        const int64_t li = i - io.row_off[g];
-        const int64_t s = li / io.nrhs;
-        const int q = (int)(li - s * io.nrhs);
-        const int32_t r = geoms[g].rows[s];
-        float2* dst = const_cast<float2*>(geoms[g].a.lam);
-        dst[li] = r >= 0 ? io.lam[g][(int64_t)r * io.ld + q] : make_float2(0.f, 0.f);
-    }
-    const int64_t outs_total = io.out_off[io.count];
-    for (int64_t i = tid; i < outs_total; i += stride) {
-        const int g = find_geom(io.out_off, io.count, i);
-        const int64_t li = i - io.out_off[g];
-        const int64_t row = li / io.nrhs;
-        const int q = (int)(li - row * io.nrhs);
-        io.out[g][row * io.ld + q] = make_float2(0.f, 0.f);
+    const int64_t n_out = io.out_off[g + 1] - io.out_off[g];
+    float2* __restrict__ out = io.out[g];
+    for (int64_t i = tid; i < n_out; i += stride) {
+        const int64_t row = i / io.nrhs;
+        const int q = (int)(i - row * io.nrhs);
+        out[row * io.ld + q] = make_float2(0.f, 0.f);
     }
 }
 
@@ -125,7 +127,6 @@ __global__ void k_batch_order(const BatchGeom* __restrict__ geoms, const int32_t
 struct BatchLayout {
     BatchGeom* geoms;
     ItemRec* order;
-    unsigned long long* counter;
     uint64_t *keys, *keys_alt;
     int32_t *vals, *vals_alt;
     void* radix_ws;
@@ -138,7 +139,6 @@ BatchLayout batch_layout(int64_t total, void* ws) {
     size_t m = (size_t)(total > 0 ? total : 1);
     L.geoms = c.take<BatchGeom>(kMaxBatch);
     L.order = c.take<ItemRec>(m);
-    L.counter = c.take<unsigned long long>(1);
     L.keys = c.take<uint64_t>(m);
     L.keys_alt = c.take<uint64_t>(m);
     L.vals = c.take<int32_t>(m);
@@ -209,12 +209,16 @@ static p2p_status batch_launch(const p2p_batch* b, const void* const* lambdas, v
         io.out[g] = static_cast<float2*>(outs[g]);
     }
     io.ld = ld;
-    const int64_t work = io.row_off[b->count] > io.out_off[b->count] ? io.row_off[b->count] : io.out_off[b->count];
+    int64_t most = 0;
+    for (int g = 0; g < b->count; ++g) {
+        most = std::max(most, io.row_off[g + 1] - io.row_off[g]);
+        most = std::max(most, io.out_off[g + 1] - io.out_off[g]);
+    }
     const int threads = 256;
-    int64_t blocks = (work + threads - 1) / threads;
-    if (blocks > 65536) blocks = 65536;
+    int64_t blocks = (most + threads - 1) / threads;
+    if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_batch_stage<<<(unsigned)blocks, threads, 0, s>>>(b->L.geoms, io, b->L.counter);
+    k_batch_stage<<<dim3((unsigned)blocks, (unsigned)b->count), threads, 0, s>>>(b->L.geoms, io);
     P2P_CHECK_LAUNCH("p2p_batch_apply/stage");
     const int smem = b->warps * b->warp_bytes;
     if (b->R == 1)

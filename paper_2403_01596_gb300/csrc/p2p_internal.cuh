@@ -23,7 +23,9 @@ struct ItemRec {
     int32_t ns;        // sources in the chunk
     int32_t tb;        // first target (box-sorted index)
     int32_t nt;        // targets of the box
-    int32_t m_end;     // the chunk's first m_end sources belong to the box itself (r = 0 possible)
+    int32_t m_end;     // low 16 bits: the chunk's first m_end sources belong to the box itself (r = 0
+                       // possible); bit 16: the chunk starts at the list's first entry, so the box's
+                       // targets t < m_end are the staged sources 0 .. m_end - 1
     int32_t map_full;  // lane map of a full target group (see p2p_lane_map)
     int32_t map_last;  // lane map of the last (possibly partial) target group
     int32_t b;         // box id

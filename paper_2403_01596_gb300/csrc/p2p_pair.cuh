@@ -267,7 +267,7 @@ __device__ __forceinline__ int map_div(int32_t m, int x) { return (x * ((int)(((
 template <int KERN, int R, int TT>
 __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* __restrict__ sx,
                                               const float2* __restrict__ sl, float2* red, int ns, int m_end,
-                                              int tbase, int nt, int32_t map, int rb, int lane) {
+                                              int tsm, int tbase, int nt, int32_t map, int rb, int lane) {
     const int G = map_g(map), Q = map_q(map);
     const int q = map_div(map, lane);
     const int g = lane - q * G;
@@ -276,7 +276,8 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
 #pragma unroll
     for (int u = 0; u < TT; ++u) {
         const int t = g + u * G;
-        tx[u] = t < nt ? a.xs[tbase + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // targets staged with the chunk (own box first) come from shared memory
+        tx[u] = t < nt ? (tsm >= 0 && tsm + t < m_end ? sx[tsm + t] : a.xs[tbase + t]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[u][r] = make_float2(0.f, 0.f);
     }
@@ -329,7 +330,8 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
 template <int KERN, int R, int TT>
 __device__ __forceinline__ void sweep_targets_sym(const PairArgs& a, const float4* __restrict__ sx,
                                                   const float2* __restrict__ sl, float2* red, float2* src_acc, int ns,
-                                                  int m_end, int tbase, int nt, int32_t map, int rb, int lane) {
+                                                  int m_end, int tsm, int tbase, int nt, int32_t map, int rb,
+                                                  int lane) {
     const int G = map_g(map), Q = map_q(map);
     const int q = map_div(map, lane);
     const int g = lane - q * G;
@@ -340,10 +342,13 @@ __device__ __forceinline__ void sweep_targets_sym(const PairArgs& a, const float
     for (int u = 0; u < TT; ++u) {
         const int t = g + u * G;
         const bool ok = t < nt && q < Q;
-        tx[u] = ok ? a.xs[tbase + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool staged = tsm >= 0 && tsm + t < m_end;  // target staged with the chunk
+        tx[u] = ok ? (staged ? sx[tsm + t] : a.xs[tbase + t]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            tl[u][r] = (ok && rb + r < a.nrhs) ? a.lam[(int64_t)(tbase + t) * a.nrhs + rb + r] : make_float2(0.f, 0.f);
+            tl[u][r] = (ok && rb + r < a.nrhs)
+                           ? (staged ? sl[(tsm + t) * R + r] : a.lam[(int64_t)(tbase + t) * a.nrhs + rb + r])
+                           : make_float2(0.f, 0.f);
             acc[u][r] = make_float2(0.f, 0.f);
         }
     }
@@ -444,16 +449,19 @@ __device__ __forceinline__ void compute_item_sym(const PairArgs& a, const ItemRe
         }
         for (int p = lane; p < r.ns * R; p += 32) src_acc[p] = make_float2(0.f, 0.f);
         __syncwarp();
+        const int m_end = r.m_end & 0xFFFF;
+        const bool first = (r.m_end >> 16) & 1;
         for (int t0 = 0; t0 < r.nt; t0 += a.tg) {
             const int nt = min(a.tg, r.nt - t0);
             const int32_t map = (t0 + a.tg >= r.nt) ? r.map_last : r.map_full;
             const int tt = map_tt(map);
-            if (tt == 1) sweep_targets_sym<KERN, R, 1>(a, st.sx, st.sl, red, src_acc, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
-            else if (tt == 2) sweep_targets_sym<KERN, R, 2>(a, st.sx, st.sl, red, src_acc, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
-            else sweep_targets_sym<KERN, R, 4>(a, st.sx, st.sl, red, src_acc, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
+            const int tsm = first ? t0 : -1;
+            if (tt == 1) sweep_targets_sym<KERN, R, 1>(a, st.sx, st.sl, red, src_acc, r.ns, m_end, tsm, r.tb + t0, nt, map, rb, lane);
+            else if (tt == 2) sweep_targets_sym<KERN, R, 2>(a, st.sx, st.sl, red, src_acc, r.ns, m_end, tsm, r.tb + t0, nt, map, rb, lane);
+            else sweep_targets_sym<KERN, R, 4>(a, st.sx, st.sl, red, src_acc, r.ns, m_end, tsm, r.tb + t0, nt, map, rb, lane);
         }
         // scatter the source-side sums of the sources outside the own box
-        for (int p = r.m_end + lane; p < r.ns; p += 32) {
+        for (int p = (r.m_end & 0xFFFF) + lane; p < r.ns; p += 32) {
             const int64_t row = (int64_t)a.perm[idx[p]] * a.ld + rb;
 #pragma unroll
             for (int q = 0; q < R; ++q) {
@@ -478,13 +486,16 @@ __device__ __forceinline__ void compute_item(const PairArgs& a, const ItemRec& r
             load_lam_block<R>(a, r, st.sl, rb, lane);
             __syncwarp();
         }
+        const int m_end = r.m_end & 0xFFFF;
+        const bool first = (r.m_end >> 16) & 1;
         for (int t0 = 0; t0 < r.nt; t0 += a.tg) {
             const int nt = min(a.tg, r.nt - t0);
             const int32_t map = (t0 + a.tg >= r.nt) ? r.map_last : r.map_full;
             const int tt = map_tt(map);
-            if (tt == 1) sweep_targets<KERN, R, 1>(a, st.sx, st.sl, red, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
-            else if (tt == 2) sweep_targets<KERN, R, 2>(a, st.sx, st.sl, red, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
-            else sweep_targets<KERN, R, 4>(a, st.sx, st.sl, red, r.ns, r.m_end, r.tb + t0, nt, map, rb, lane);
+            const int tsm = first ? t0 : -1;
+            if (tt == 1) sweep_targets<KERN, R, 1>(a, st.sx, st.sl, red, r.ns, m_end, tsm, r.tb + t0, nt, map, rb, lane);
+            else if (tt == 2) sweep_targets<KERN, R, 2>(a, st.sx, st.sl, red, r.ns, m_end, tsm, r.tb + t0, nt, map, rb, lane);
+            else sweep_targets<KERN, R, 4>(a, st.sx, st.sl, red, r.ns, m_end, tsm, r.tb + t0, nt, map, rb, lane);
         }
     }
 }

@@ -215,7 +215,7 @@ __global__ void k_item_records(const int32_t* __restrict__ n_chunks, const int32
         r.ns = min(chunk, S - s0);
         r.tb = tb;
         r.nt = nt;
-        r.m_end = max(0, min(r.ns, nt - s0));
+        r.m_end = max(0, min(r.ns, nt - s0)) | (s0 == 0 ? (1 << 16) : 0);
         r.map_full = p2p_lane_map(min(nt, tg), r.ns);
         r.map_last = p2p_lane_map(last, r.ns);
         r.b = b;
