@@ -16,12 +16,13 @@ namespace {
 // Persistent pair kernel: warp w of the grid takes items w, w + W, w + 2W, ...
 // of the plan's heaviest-first item list (W = warps in the grid).
 template <int R>
-__global__ void __launch_bounds__(512, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1) k_pair(const __grid_constant__ PairArgs a) {
+__global__ void __launch_bounds__(P2P_PAIR_MAX_THREADS, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1)
+    k_pair(const __grid_constant__ PairArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int warps = blockDim.x >> 5;
-    unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(a.chunk, R);
-    run_pipeline<R>(ws, a.chunk, lane, a.items, a.n_items, (int64_t)blockIdx.x * warps + warp,
+    unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(a.chunk, R, a.sym);
+    run_pipeline<R>(ws, a.chunk, a.sym != 0, lane, a.items, a.n_items, (int64_t)blockIdx.x * warps + warp,
                     (int64_t)gridDim.x * warps, a.status, [&](const ItemRec&) -> const PairArgs* { return &a; });
 }
 
@@ -215,10 +216,14 @@ cudaError_t configure_r(p2p_plan* p) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // the tuning's warps per block, halved until one block's shared memory fits
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_pair<R>);
+    if (e != cudaSuccess) return e;
+    const bool sym = p->layout == P2P_LAYOUT_SYMMETRIC;
+    // the tuning's warps per block, halved until one block fits (threads, shared memory)
     for (int warps = p->tune.warps_per_cta; warps >= 1; warps >>= 1) {
-        const int smem = warps * warp_smem_bytes(p->tune.chunk, R);
-        if (smem > optin) continue;
+        const int smem = warps * warp_smem_bytes(p->tune.chunk, R, sym);
+        if (smem > optin || warps * 32 > fa.maxThreadsPerBlock) continue;
         e = raise_smem_limit<R>(smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
@@ -236,7 +241,7 @@ cudaError_t configure_r(p2p_plan* p) {
 template <int R>
 p2p_status launch_pair(const p2p_plan* p, const PairArgs& a, cudaStream_t s) {
     const int warps = p->grid_warps[r_index(R)];
-    const int smem = warps * warp_smem_bytes(a.chunk, R);
+    const int smem = warps * warp_smem_bytes(a.chunk, R, a.sym != 0);
     int grid = p->grid[r_index(R)];
     if (grid <= 0) {
         set_message("p2p_apply: the pair kernel does not fit on this device with this tuning (shared memory)");
@@ -265,9 +270,10 @@ cudaError_t p2p_pair_configure(p2p_plan* plan) {
     return e;
 }
 
-// Entry shared with the tensor-core translation unit.
-p2p_status p2p_apply_tc(const p2p_plan* plan, const float2* lam_sorted, float2* out, int32_t nrhs, int64_t ld,
-                        int32_t adjoint, cudaStream_t s);
+// Entries shared with the tensor-core translation unit.
+p2p_status p2p_tc_stage(const p2p_plan* plan, const float2* lam, int32_t nrhs, int64_t ld, cudaStream_t s);
+p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t ld, int32_t adjoint,
+                        cudaStream_t s);
 bool p2p_tc_supported(const p2p_plan* plan, int32_t nrhs);
 
 extern "C" {
@@ -287,7 +293,8 @@ P2P_API p2p_status p2p_apply_stage(const p2p_plan* plan, const void* lambda, int
     path = resolve_path(plan, nrhs, path);
     if (path == P2P_PATH_TC_BF16X3 && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool red = plan->layout == P2P_LAYOUT_REDUNDANT && path != P2P_PATH_TC_BF16X3;
+    if (path == P2P_PATH_TC_BF16X3) return p2p_tc_stage(plan, (const float2*)lambda, nrhs, ld, s);
+    const bool red = plan->layout == P2P_LAYOUT_REDUNDANT;
     const int32_t* rows = red ? plan->pk_src : plan->perm;
     const int64_t nrows = red ? plan->packed : plan->n;
     P2P_TRY_CUDA(stage_rows((const float2*)lambda, ld, rows, nrows, nrhs, plan->lam_buf, s), "p2p_apply_stage");
@@ -303,7 +310,7 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
     path = resolve_path(plan, nrhs, path);
     if (path == P2P_PATH_TC_BF16X3 && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
-    if (path == P2P_PATH_TC_BF16X3) return p2p_apply_tc(plan, plan->lam_buf, (float2*)out, nrhs, ld, adjoint, s);
+    if (path == P2P_PATH_TC_BF16X3) return p2p_apply_tc(plan, (float2*)out, nrhs, ld, adjoint, s);
     PairArgs a = base_args(plan);
     a.out = (float2*)out;
     a.ld = ld;

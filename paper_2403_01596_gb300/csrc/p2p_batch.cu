@@ -89,14 +89,14 @@ __global__ void k_batch_stage(BatchGeom* __restrict__ geoms, const BatchIO io) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(512, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1) k_pair_batched(const BatchGeom* __restrict__ geoms,
-                                                                                         const ItemRec* __restrict__ recs,
-                                                                                         int64_t total, int chunk_max) {
+__global__ void __launch_bounds__(P2P_PAIR_MAX_THREADS, R == 1 ? P2P_PAIR_MIN_BLOCKS : 1)
+    k_pair_batched(const BatchGeom* __restrict__ geoms, const ItemRec* __restrict__ recs, int64_t total, int chunk_max,
+                   int sym_any) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int warps = blockDim.x >> 5;
-    unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(chunk_max, R);
-    run_pipeline<R>(ws, chunk_max, lane, recs, total, (int64_t)blockIdx.x * warps + warp, (int64_t)gridDim.x * warps,
+    unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(chunk_max, R, sym_any != 0);
+    run_pipeline<R>(ws, chunk_max, sym_any != 0, lane, recs, total, (int64_t)blockIdx.x * warps + warp, (int64_t)gridDim.x * warps,
                     geoms[0].a.status, [&](const ItemRec& r) -> const PairArgs* { return &geoms[r.b].a; });
 }
 
@@ -159,7 +159,10 @@ cudaError_t configure(int warps, int warp_bytes, int* ctas_per_sm) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if (smem > optin) {
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_pair_batched<R>);
+    if (e != cudaSuccess) return e;
+    if (smem > optin || warps * 32 > fa.maxThreadsPerBlock) {
         *ctas_per_sm = 0;
         return cudaSuccess;
     }
@@ -177,6 +180,7 @@ struct p2p_batch {
     int32_t warps;
     int32_t warp_bytes;
     int32_t chunk_max;
+    int32_t sym_any;        // some geometry uses the symmetric layout (per-warp source accumulator)
     int32_t grid;
     int64_t total;
     const p2p_plan* plans[kMaxBatch];
@@ -222,11 +226,11 @@ static p2p_status batch_launch(const p2p_batch* b, const void* const* lambdas, v
     P2P_CHECK_LAUNCH("p2p_batch_apply/stage");
     const int smem = b->warps * b->warp_bytes;
     if (b->R == 1)
-        k_pair_batched<1><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->chunk_max);
+        k_pair_batched<1><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->chunk_max, b->sym_any);
     else if (b->R == 2)
-        k_pair_batched<2><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->chunk_max);
+        k_pair_batched<2><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->chunk_max, b->sym_any);
     else
-        k_pair_batched<4><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->chunk_max);
+        k_pair_batched<4><<<b->grid, b->warps * 32, smem, s>>>(b->L.geoms, b->L.order, b->total, b->chunk_max, b->sym_any);
     P2P_CHECK_LAUNCH("p2p_batch_apply/pair");
     return P2P_OK;
 }
@@ -282,12 +286,13 @@ P2P_API p2p_status p2p_batch_create(p2p_batch** batch, const p2p_plan* const* pl
         host[g].nrows = host[g].a.red ? p->packed : p->n;
         host[g].rows = host[g].a.red ? p->pk_src : p->perm;
         max_chunk = std::max(max_chunk, p->tune.chunk);
+        if (host[g].a.sym) b->sym_any = 1;
         off.off[g + 1] = off.off[g] + p->n_items;
         b->io.row_off[g + 1] = b->io.row_off[g] + host[g].nrows * nrhs;
         b->io.out_off[g + 1] = b->io.out_off[g] + (host[g].a.atomic_out ? p->n * nrhs : 0);
     }
     b->chunk_max = max_chunk;
-    b->warp_bytes = warp_smem_bytes(max_chunk, b->R);
+    b->warp_bytes = warp_smem_bytes(max_chunk, b->R, b->sym_any != 0);
 #define FAIL(expr, where)                 \
     do {                                  \
         cudaError_t e_ = (expr);          \

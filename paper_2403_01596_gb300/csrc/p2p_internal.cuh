@@ -92,7 +92,23 @@ struct p2p_plan {
     float2* g_buf;          // [n * max_nrhs] sorted upstream gradient (coordinate gradient)
     unsigned int* status;   // device status word
     long long* scratch64;   // small device scratch (pair count)
+    // tensor-core path (plans with max_nrhs >= 16)
+    int32_t* tc_gstart;     // [nb + 1] first 16-source group of every box (exclusive scan of ceil(n_b / 16))
+    int32_t tc_groups;      // number of 16-source groups
+    int32_t* tc_glist_off;  // [nb + 1] offsets of the per-box group lists
+    int32_t* tc_glist;      // per box: the groups of its neighbour boxes (ascending box id), -1 padding to a
+                            // multiple of 4 entries
+    int32_t* tc_gcount;     // [nb] groups in the list of every box (without padding)
+    unsigned char* tc_pack; // per-apply group records: BF16 hi/lo strength images (one per block of 64 RHS)
+                            // followed by the group's 16 source coordinates
 };
+
+// Bytes of the tensor-core group records for n points in nb boxes (0 when max_nrhs < 16).
+size_t p2p_tc_pack_bytes(int64_t n, int32_t nb, int32_t max_nrhs);
+// Entries of the tensor-core group lists: at most sources / 16 + nnz + 3 nb.
+inline size_t p2p_tc_list_bound(int64_t sources, int64_t nnz, int32_t nb) {
+    return (size_t)(sources / 16 + nnz + 3 * (int64_t)nb + 4);
+}
 
 namespace p2p_detail {
 

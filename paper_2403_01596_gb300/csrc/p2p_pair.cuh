@@ -29,11 +29,15 @@
 
 #include "p2p_internal.cuh"
 
-// Unroll factor of the per-lane source loop, and the minimum number of
-// resident 512-thread blocks the pair kernel is compiled for (its register
-// budget: 65536 / (512 * P2P_PAIR_MIN_BLOCKS) registers per thread).
+// Unroll factor of the per-lane source loop, and the launch bounds the pair
+// kernel is compiled for: blocks of at most P2P_PAIR_MAX_THREADS threads, at
+// least P2P_PAIR_MIN_BLOCKS of them resident (its register budget:
+// 65536 / (P2P_PAIR_MAX_THREADS * P2P_PAIR_MIN_BLOCKS) registers per thread).
 #ifndef P2P_PAIR_UNROLL
 #define P2P_PAIR_UNROLL 2
+#endif
+#ifndef P2P_PAIR_MAX_THREADS
+#define P2P_PAIR_MAX_THREADS 512
 #endif
 #ifndef P2P_PAIR_MIN_BLOCKS
 #define P2P_PAIR_MIN_BLOCKS 1
@@ -72,11 +76,11 @@ struct PairArgs {
 // Per-warp shared memory: two data stages (coordinates + R strengths per
 // source), three index stages (the chunk's source list; an item's list stays
 // until its results are scattered), the slice-reduction buffer, the source-side
-// accumulator of the symmetric layout, and five mbarriers (two for data, three
+// accumulator (symmetric layout only), and five mbarriers (two for data, three
 // for indices).
 __host__ __device__ inline int stage_bytes(int chunk, int R) { return chunk * 16 + chunk * R * 8; }
-__host__ __device__ inline int warp_smem_bytes(int chunk, int R) {
-    return 2 * stage_bytes(chunk, R) + 3 * chunk * 4 + 32 * kMaxTT * R * 8 + chunk * R * 8 + 48;
+__host__ __device__ inline int warp_smem_bytes(int chunk, int R, bool sym) {
+    return 2 * stage_bytes(chunk, R) + 3 * chunk * 4 + 32 * kMaxTT * R * 8 + (sym ? chunk * R * 8 : 0) + 48;
 }
 
 // ------------------------------------------------------------ async copies --
@@ -144,7 +148,7 @@ struct WarpSmem {
     __device__ __forceinline__ int* index(int i) const { return idx + i * chunk; }
 };
 
-__device__ __forceinline__ WarpSmem warp_smem(unsigned char* ws, int chunk, int R) {
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char* ws, int chunk, int R, bool sym) {
     WarpSmem w;
     w.chunk = chunk;
     w.R = R;
@@ -155,7 +159,7 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char* ws, int chunk, int 
     w.red = reinterpret_cast<float2*>(q);
     q += 32 * kMaxTT * R * 8;
     w.src_acc = reinterpret_cast<float2*>(q);
-    q += chunk * R * 8;
+    if (sym) q += chunk * R * 8;
     w.bar = reinterpret_cast<uint64_t*>(q);
     return w;
 }
@@ -231,13 +235,17 @@ __device__ __forceinline__ void pair_step(const float4* __restrict__ sx, const f
 #pragma unroll
     for (int u = 0; u < TT; ++u) {
         const float dx = p.x - tx[u].x, dy = p.y - tx[u].y, dz = p.z - tx[u].z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float inv;
+        float r2, inv;
         if (MASK) {
+            r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             inv = rsqrtf(r2);
             inv = r2 > 0.f ? inv : 0.f;
         } else {
-            inv = rsqrtf(fmaxf(r2, 1.17549435e-38f));
+            // sources of other boxes are never at r = 0; starting the sum at the
+            // smallest normal float keeps r^2 positive (rsqrt finite) even when the
+            // squares of a very close pair underflow, at no extra instruction
+            r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1.17549435e-38f)));
+            inv = rsqrtf(r2);
         }
         if (KERN == P2P_HELMHOLTZ) {
             float sn, cs;
@@ -371,8 +379,8 @@ __device__ __forceinline__ void sweep_targets_sym(const PairArgs& a, const float
 #pragma unroll
             for (int u = 0; u < TT; ++u) {
                 const float dx = p.x - tx[u].x, dy = p.y - tx[u].y, dz = p.z - tx[u].z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float inv = rsqrtf(fmaxf(r2, 1.17549435e-38f));
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1.17549435e-38f)));
+                const float inv = rsqrtf(r2);
                 float gr = inv, gi = 0.f;
                 if (KERN == P2P_HELMHOLTZ) {
                     float sn, cs;
@@ -538,9 +546,9 @@ __device__ __forceinline__ ItemRec gather_rec(int32_t v) {
 // (k+1) % 2), then waits for item k's data and sweeps it.  Every mbarrier wait
 // is bounded.
 template <int R, typename ArgsOf>
-__device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, int lane, const ItemRec* items, int64_t n,
+__device__ __forceinline__ void run_pipeline(unsigned char* ws, int chunk, bool sym, int lane, const ItemRec* items, int64_t n,
                                              int64_t first, int64_t stride, unsigned int* status, ArgsOf args_of) {
-    const WarpSmem w = warp_smem(ws, chunk, R);
+    const WarpSmem w = warp_smem(ws, chunk, R, sym);
     if (lane == 0) {
 #pragma unroll
         for (int i = 0; i < 5; ++i) mbar_init(&w.bar[i]);

@@ -231,6 +231,42 @@ __global__ void k_item_gather(const ItemRec* __restrict__ recs, const int32_t* _
     if (i < n) out[i] = recs[order[i]];
 }
 
+// Source groups of the tensor-core path: ceil(n_b / 16) per box.
+__global__ void k_tc_groups(const int32_t* __restrict__ box_ptr, int32_t nb, int32_t* __restrict__ groups) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) groups[b] = (box_ptr[b + 1] - box_ptr[b] + 15) / 16;
+}
+
+// Length of every box's group list: the groups of its neighbour boxes, and that
+// count padded to a multiple of 4.
+__global__ void k_tc_list_len(const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr_idx,
+                              const int32_t* __restrict__ gstart, int32_t nb, int32_t* __restrict__ count,
+                              int32_t* __restrict__ padded) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int g = 0;
+    for (int e = nbr_ptr[b]; e < nbr_ptr[b + 1]; ++e) {
+        const int c = nbr_idx[e];
+        g += gstart[c + 1] - gstart[c];
+    }
+    count[b] = g;
+    padded[b] = (g + 3) & ~3;
+}
+
+// Group lists: neighbour boxes in ascending id, each box's groups in order, -1 padding.
+__global__ void k_tc_list_fill(const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr_idx,
+                               const int32_t* __restrict__ gstart, const int32_t* __restrict__ off, int32_t nb,
+                               int32_t* __restrict__ list) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int o = off[b];
+    for (int e = nbr_ptr[b]; e < nbr_ptr[b + 1]; ++e) {
+        const int c = nbr_idx[e];
+        for (int g = gstart[c]; g < gstart[c + 1]; ++g) list[o++] = g;
+    }
+    while (o < off[b + 1]) list[o++] = -1;
+}
+
 // One warp per box: writes the box's source list -- the box's own sources
 // first, then the other neighbour boxes in ascending id (the order the pair
 // kernel's r = 0 mask relies on) -- as box-sorted indices (nb_src, the index
@@ -397,7 +433,7 @@ struct PlanLayout {
     size_t bytes;
 };
 
-PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, p2p_layout layout, int32_t max_nrhs,
+PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, int64_t nnz, p2p_layout layout, int32_t max_nrhs,
                        const p2p_tuning& t, void* ws) {
     Carver c{static_cast<char*>(ws), 0, (size_t)-1};
     PlanLayout L;
@@ -420,6 +456,12 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, p2p_layout layout
     const size_t lam_bytes = lam_rows * (size_t)max_nrhs * sizeof(float2);
     L.p.lam_buf = c.take<float2>(lam_rows * (size_t)max_nrhs);
     L.p.g_buf = c.take<float2>(m * (size_t)max_nrhs);
+    const size_t tc_bytes = p2p_tc_pack_bytes((int64_t)m, (int32_t)mb, max_nrhs);
+    L.p.tc_gstart = tc_bytes ? c.take<int32_t>(mb + 1) : nullptr;
+    L.p.tc_glist_off = tc_bytes ? c.take<int32_t>(mb + 1) : nullptr;
+    L.p.tc_gcount = tc_bytes ? c.take<int32_t>(mb) : nullptr;
+    L.p.tc_glist = tc_bytes ? c.take<int32_t>(p2p_tc_list_bound(sources, nnz, (int32_t)mb)) : nullptr;
+    L.p.tc_pack = tc_bytes ? c.take<unsigned char>(tc_bytes) : nullptr;
     L.n_chunks = c.take<int32_t>(mb);
     L.list_len = c.take<int32_t>(mb);
     L.item_off = c.take<int32_t>(mb + 1);
@@ -574,7 +616,7 @@ P2P_API p2p_status p2p_plan_workspace_size(int64_t n, int32_t num_boxes, int64_t
         return P2P_ERR_INVALID;
     p2p_tuning t = resolve_tuning(tuning);
     if (!tuning_valid(t)) return P2P_ERR_INVALID;
-    *bytes = plan_layout(n, num_boxes, sources, layout, max_nrhs, t, nullptr).bytes;
+    *bytes = plan_layout(n, num_boxes, sources, nnz, layout, max_nrhs, t, nullptr).bytes;
     return P2P_OK;
 }
 
@@ -597,7 +639,7 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
     if (workspace_bytes < need) return P2P_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     p2p_tuning t = resolve_tuning(tuning);
-    PlanLayout L = plan_layout(n, num_boxes, sources, layout, max_nrhs, t, workspace);
+    PlanLayout L = plan_layout(n, num_boxes, sources, nnz, layout, max_nrhs, t, workspace);
     p2p_plan* p = (p2p_plan*)malloc(sizeof(p2p_plan));
     if (!p) return P2P_ERR_ALLOC;
     *p = L.p;
@@ -652,14 +694,33 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
                                                                         p->pk_off, num_boxes, t.chunk, t.target_group,
                                                                         L.recs, L.keys, L.vals);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/items");
+    if (p->tc_gstart) {
+        // 16-source groups of the tensor-core path (n_chunks is free once the items are built)
+        k_tc_groups<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(box_ptr, num_boxes, L.n_chunks);
+        FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/tc_groups");
+        FAIL_CUDA(scan_exclusive_i32(L.n_chunks, p->tc_gstart, num_boxes, p->tc_gstart + num_boxes, L.scan_ws, s),
+                  "p2p_plan_create/tc_scan");
+        k_tc_list_len<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(nbr_ptr, nbr_idx, p->tc_gstart, num_boxes,
+                                                                            p->tc_gcount, L.n_chunks);
+        FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/tc_lists");
+        FAIL_CUDA(scan_exclusive_i32(L.n_chunks, p->tc_glist_off, num_boxes, p->tc_glist_off + num_boxes, L.scan_ws, s),
+                  "p2p_plan_create/tc_scan");
+        k_tc_list_fill<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(nbr_ptr, nbr_idx, p->tc_gstart,
+                                                                             p->tc_glist_off, num_boxes, p->tc_glist);
+        FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/tc_lists");
+    }
     int32_t host[4] = {0, 0, 0, 0};
     unsigned int status = 0;
     int32_t packed = 0;
+    int32_t tc_groups = 0;
     FAIL_CUDA(cudaMemcpyAsync(host, L.maxes, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
     FAIL_CUDA(cudaMemcpyAsync(host + 2, L.small, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
     FAIL_CUDA(cudaMemcpyAsync(&status, p->status, sizeof(status), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
     FAIL_CUDA(cudaMemcpyAsync(&packed, p->pk_off + num_boxes, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
               "p2p_plan_create");
+    if (p->tc_gstart)
+        FAIL_CUDA(cudaMemcpyAsync(&tc_groups, p->tc_gstart + num_boxes, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                  "p2p_plan_create");
     FAIL_CUDA(cudaStreamSynchronize(s), "p2p_plan_create");
     if (!status) {
         const int64_t items = host[2];
@@ -681,6 +742,7 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
     p->max_box = host[1];
     p->n_items = host[2];
     p->packed = packed;
+    p->tc_groups = tc_groups;
     FAIL_CUDA(p2p_pair_configure(p), "p2p_plan_create/occupancy");
 #undef FAIL_CUDA
     *plan = p;

@@ -1,26 +1,51 @@
 // Multi-RHS P2P on the 5th-generation tensor cores (tcgen05, TMEM accumulator).
 //
-// For one target box b and a group of at most 64 of its targets, the complex
-// product out[t, r] = sum_s G(x_t, y_s) lambda[s, r] over the box's
-// neighbourhood is computed as one real GEMM per 32-source stage,
+// Contraction.  A unit of work is one target box b and a group of nt <= TG of
+// its targets (T = nt rounded up to 8).  For every group of 16 consecutive
+// box-sorted sources of a neighbour box, one real MMA chain adds
 //
-//     D[128 x N] += A[128 x 64] . B[64 x N],
-//     A[2t, 2s] = Re G, A[2t, 2s+1] = -Im G, A[2t+1, 2s] = Im G, A[2t+1, 2s+1] = Re G,
-//     B[2s, r] = Re lambda[s, r],  B[2s+1, r] = Im lambda[s, r],
+//     D[128 x 2T] += A[128 x 16] . B[16 x 2T],
+//     A[r, s] = Re lambda[s, r],  A[64 + r, s] = Im lambda[s, r]   (r: RHS within a block of 64)
+//     B[s, t] = Re G(x_t, y_s),   B[s, T + t]  = Im G(x_t, y_s),
 //
-// so that D[2t, r] = Re out[t, r] and D[2t+1, r] = Im out[t, r].  The G tile is
-// formed on the CUDA cores (rsqrt, sincos in FP32), both operands are split
-// x = hi + lo into BF16, and three MMAs per K = 16 slice (hi.hi + hi.lo + lo.hi,
-// kind::f16, FP32 accumulate in TMEM) keep the product error near 2^-17.  Two
-// shared-memory stages alternate: CUDA cores fill one while the tensor core
-// reads the other; tcgen05.commit on an mbarrier releases a stage.  Every wait
-// is bounded: a wait that runs out sets the plan's status word and the CTA
-// drains its MMAs (again bounded), frees its TMEM and returns.
+// so that Re out[t, r] = D[r, t] - D[64 + r, T + t] and Im out[t, r] =
+// D[r, T + t] + D[64 + r, t] (the four real products of a complex product; no
+// padded M rows and no negated copy).  G is formed on the CUDA cores in FP32
+// (rsqrt, sincos), both operands are split x = hi + lo into BF16, and three MMAs
+// (hi.hi + hi.lo + lo.hi, kind::f16, FP32 accumulation in TMEM) keep the product
+// error near 2^-16.
+//
+// Group records.  The A operand of a source group does not depend on the target
+// box, so a pass per apply (k_tc_pack) writes every group's hi and lo images,
+// already in the operand's shared-memory layout, followed by the group's source
+// coordinates; the main kernel moves a record with one TMA bulk copy.  The plan
+// keeps, per box, the list of the groups of its neighbour boxes (ascending box
+// id), padded with -1 to a multiple of four entries.
+//
+// Main kernel (k_p2p_tc): persistent, one CTA per SM, units (box, target group)
+// round robin over the CTAs in Morton order (neighbouring CTAs share records in
+// L2).  Warp roles:
+//   warp 0       producer: walks a unit's group list four entries at a time; lane s issues entry 4q + s
+//                into a slot of G set s (metadata, TMA bulk copy of the record, the unit's targets with
+//                the first quad)
+//   warps 1-16   four G sets of four warps: G tile in FP32, BF16 hi/lo split into the slot's B operand;
+//                after a set-wide named barrier the set's first thread issues the three MMAs (per RHS
+//                block) into the set's own accumulator and commits them to the slot's release barrier
+//   warps 17-20  epilogue: sums the sets' accumulators (TMEM -> registers), combines Re/Im through
+//                shared memory and writes out[perm[t]]
+// Four independent issue chains (one per set) keep the tensor core fed with the
+// small (N = 2T) MMAs; two TMEM buffers alternate between a CTA's units so the
+// epilogue of one unit overlaps the MMAs of the next.
+//
+// Every wait is bounded: a wait that runs out sets the plan's status word and an
+// abort flag; every role then stops (the warps of a set or of the epilogue decide
+// together through a barrier reduction), the producer waits (bounded) for the
+// bulk copies it issued, each set's issuing thread for its MMAs, and the CTA
+// frees its TMEM and returns.
 //
 // Operands use the canonical K-major layout without swizzle: 8-row x 16-byte
-// core matrices, K-adjacent cores 128 bytes apart (leading byte offset) and
-// 8-row groups kCoreStride bytes apart (stride byte offset; 1024 + 16 so that
-// the 16-byte stores of eight consecutive rows hit distinct bank groups).
+// core matrices, the two K-adjacent cores of a 16-wide K slice 128 bytes apart
+// (leading byte offset) and 8-row groups 256 bytes apart (stride byte offset).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -31,17 +56,16 @@ using namespace p2p_detail;
 namespace {
 
 constexpr float kInv4Pi = 0.0795774715459476679f;
-constexpr int kTcThreads = 128;
-constexpr int kTcTargets = 64;        // targets per CTA (128 accumulator rows)
-constexpr int kTcStageSrc = 32;       // sources per stage (K = 64)
-constexpr int kCoreStride = 1040;     // bytes between 8-row core groups
-constexpr int kATile = 16 * kCoreStride;
-constexpr uint32_t kWaitLimit = 1u << 24;
-
-__host__ __device__ inline int b_tile_bytes(int np) { return (np / 8) * kCoreStride; }
-__host__ __device__ inline int stage_bytes(int np) { return 2 * kATile + 2 * b_tile_bytes(np); }
-constexpr int kExtraBytes = 64 * 16 + 32 * 16 + 32 * 4 + 64 * 4 + 2 * 8 + 16;
-__host__ __device__ inline int tc_smem_bytes(int np) { return 2 * stage_bytes(np) + kExtraBytes; }
+constexpr int kSrcGroup = 16;          // sources per stage (MMA K)
+constexpr int kImage = 8192;           // hi + lo images of one 128 x 16 A operand
+constexpr int kLbo = 128, kSbo = 256;  // core-matrix strides (K direction, 8-row groups)
+constexpr int kSetCols = 256;          // TMEM columns of one unit buffer (an accumulator per G set)
+constexpr int kSets = 4;               // G sets of four warps; set s takes list entries s, s + kSets, ...
+constexpr int kGWarp0 = 1, kEpiWarp0 = kGWarp0 + 4 * kSets;
+constexpr int kWarps = kEpiWarp0 + 4;
+constexpr int kThreads = kWarps * 32;
+constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kDrainLimit = 1u << 16;
 
 // --------------------------------------------------------------- PTX helpers --
 
@@ -49,8 +73,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 
 // Shared-memory matrix descriptor: start, leading and stride byte offsets (>> 4),
 // descriptor version 1 at bit 46, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kLbo >> 4) << 16) | ((uint64_t)(kSbo >> 4) << 32) |
            (1ull << 46);
 }
 
@@ -63,20 +87,41 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t addr = smem_u32(bar);
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait; gives up early once *abort is set.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          uint32_t limit = kWaitLimit) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if (abort && (i & 255u) == 255u && *abort) return false;
     }
     return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -107,6 +152,32 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Named barriers: 1 .. 4 for the G sets, 5 for the epilogue warps (0 is __syncthreads).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 5, 128;" ::: "memory"); }
+// Barrier of the 128 epilogue threads that also ORs a condition over them.
+__device__ __forceinline__ bool epi_any(bool c) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 5, 128, q;\n\t"
+        "selp.s32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((int)c)
+        : "memory");
+    return r != 0;
+}
+
+// 32 lanes x 8 consecutive 32-bit columns of TMEM into registers.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 // 32 lanes x 16 consecutive 32-bit columns of TMEM into registers.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -122,7 +193,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// x = hi + lo with hi, lo BF16 (round to nearest).
+// x = hi + lo with hi, lo BF16 (round to nearest), two values per 32-bit word.
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     float2 hf = __bfloat1622float2(h);
@@ -131,364 +202,614 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
     lo = *reinterpret_cast<uint32_t*>(&l);
 }
 
-// Splits 8 floats (one 16-byte core-matrix row) and stores hi and lo rows.
-__device__ __forceinline__ void store_split8(unsigned char* hi_base, unsigned char* lo_base, int off,
-                                             const float (&v)[8]) {
-    uint4 h, l;
-    split2(v[0], v[1], h.x, l.x);
-    split2(v[2], v[3], h.y, l.y);
-    split2(v[4], v[5], h.z, l.z);
-    split2(v[6], v[7], h.w, l.w);
-    *reinterpret_cast<uint4*>(hi_base + off) = h;
-    *reinterpret_cast<uint4*>(lo_base + off) = l;
+__device__ __forceinline__ void split1(float a, uint16_t& hi, uint16_t& lo) {
+    __nv_bfloat16 h = __float2bfloat16_rn(a);
+    __nv_bfloat16 l = __float2bfloat16_rn(a - __bfloat162float(h));
+    hi = *reinterpret_cast<uint16_t*>(&h);
+    lo = *reinterpret_cast<uint16_t*>(&l);
 }
 
-__device__ __forceinline__ int core_off(int row, int kc) { return (row >> 3) * kCoreStride + kc * 128 + (row & 7) * 16; }
+// Byte offset of element (row, k) of a K-major operand with 16-wide K slices.
+__host__ __device__ inline int op_off(int row, int k) {
+    return (row >> 3) * kSbo + (k >> 3) * kLbo + (row & 7) * 16 + (k & 7) * 2;
+}
 
-// Issues the three MMAs of every K = 16 slice of one stage (single thread).
-__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
-                                            uint32_t idesc, bool first) {
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t ah = smem_desc(a_hi + kk * 256, 128, kCoreStride);
-        const uint64_t al = smem_desc(a_lo + kk * 256, 128, kCoreStride);
-        const uint64_t bh = smem_desc(b_hi + kk * 256, 128, kCoreStride);
-        const uint64_t bl = smem_desc(b_lo + kk * 256, 128, kCoreStride);
-        mma_bf16(tmem, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
-        mma_bf16(tmem, ah, bl, idesc, 1u);
-        mma_bf16(tmem, al, bh, idesc, 1u);
+// Splits n values (n = 1, 2, 4 or 8, consecutive K elements of one row) and
+// stores the hi and lo parts.
+template <int N>
+__device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo, int off, const float (&v)[N]) {
+    if constexpr (N == 1) {
+        uint16_t h, l;
+        split1(v[0], h, l);
+        *reinterpret_cast<uint16_t*>(hi + off) = h;
+        *reinterpret_cast<uint16_t*>(lo + off) = l;
+    } else if constexpr (N == 2) {
+        uint32_t h, l;
+        split2(v[0], v[1], h, l);
+        *reinterpret_cast<uint32_t*>(hi + off) = h;
+        *reinterpret_cast<uint32_t*>(lo + off) = l;
+    } else if constexpr (N == 4) {
+        uint2 h, l;
+        split2(v[0], v[1], h.x, l.x);
+        split2(v[2], v[3], h.y, l.y);
+        *reinterpret_cast<uint2*>(hi + off) = h;
+        *reinterpret_cast<uint2*>(lo + off) = l;
+    } else {
+        uint4 h, l;
+        split2(v[0], v[1], h.x, l.x);
+        split2(v[2], v[3], h.y, l.y);
+        split2(v[4], v[5], h.z, l.z);
+        split2(v[6], v[7], h.w, l.w);
+        *reinterpret_cast<uint4*>(hi + off) = h;
+        *reinterpret_cast<uint4*>(lo + off) = l;
     }
 }
 
+// ----------------------------------------------------------- strength pre-pack --
+
+// Bytes of one group record: the hi and lo images of every block of 64 RHS,
+// then the group's 16 source coordinates (w = 1 marks a padding slot).
+__host__ __device__ inline int record_bytes(int rb_count) { return rb_count * kImage + kSrcGroup * 16; }
+
+// Block (group g, RHS block rb), 128 threads: thread (r = tid % 64, o = tid / 64)
+// splits Re and Im lambda of RHS rb * 64 + r for sources 8o .. 8o + 7 of the
+// group into rows r and 64 + r of the group's hi and lo images.  Sources past the
+// box's end and RHS past nrhs are zero.  Block row rb = 0 also writes the
+// coordinates.
+__global__ void __launch_bounds__(128) k_tc_pack(const float2* __restrict__ lam, int64_t ld, int32_t nrhs,
+                                                 const int32_t* __restrict__ perm, const int32_t* __restrict__ box_ptr,
+                                                 const float4* __restrict__ xs, const int32_t* __restrict__ gstart,
+                                                 int32_t nb, int32_t rb_count, unsigned char* __restrict__ pack) {
+    const int g = blockIdx.x, rb = blockIdx.y;
+    // box of group g: the last c with gstart[c] <= g
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gstart[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const int c = lo;
+    const int j = g - gstart[c];
+    const int s0 = box_ptr[c] + j * kSrcGroup;
+    const int cnt = min(kSrcGroup, box_ptr[c + 1] - s0);
+    unsigned char* rec = pack + (int64_t)g * record_bytes(rb_count);
+    if (rb == 0 && threadIdx.x < kSrcGroup) {
+        const int k = threadIdx.x;
+        reinterpret_cast<float4*>(rec + rb_count * kImage)[k] = k < cnt ? xs[s0 + k] : make_float4(0.f, 0.f, 0.f, 1.f);
+    }
+    const int r = threadIdx.x & 63, o = threadIdx.x >> 6;
+    const int rr = rb * 64 + r;
+    float re[8], im[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = 8 * o + e;
+        float2 v = make_float2(0.f, 0.f);
+        if (k < cnt && rr < nrhs) v = lam[(int64_t)perm[s0 + k] * ld + rr];
+        re[e] = v.x;
+        im[e] = v.y;
+    }
+    unsigned char* img = rec + rb * kImage;
+    store_split<8>(img, img + kImage / 2, op_off(r, 8 * o), re);
+    store_split<8>(img, img + kImage / 2, op_off(64 + r, 8 * o), im);
+}
+
+// ------------------------------------------------------------------ main kernel --
+
 struct TcArgs {
-    const float4* xs;
-    const float2* lam;     // box-sorted strengths, row stride nrhs
+    const float4* xs;              // box-sorted coordinates
+    const unsigned char* pack;     // group records
     const int32_t* box_ptr;
-    const int32_t* nbr_ptr;
-    const int32_t* nbr_idx;
-    const int32_t* box_src;
+    const int32_t* glist_off;      // per-box group lists (padded to multiples of kSets)
+    const int32_t* glist;
+    const int32_t* gcount;
     const int32_t* perm;
     float2* out;
     int64_t ld;
     int32_t nrhs;
-    int32_t np;            // nrhs rounded up to a multiple of 16 (MMA N)
-    int32_t nacc;          // TMEM accumulators the stages rotate over (1, 2 or 4)
-    int32_t tmem_cols;
-    int32_t laplace;
+    int32_t rb_count;              // RHS blocks of 64
+    int32_t tg;                    // targets per unit (multiple of 8)
+    int32_t ngrp;                  // units per box: ceil(max_box / tg)
+    int32_t nb;
+    int32_t slots;                 // pipeline slots per G set
+    int32_t slot_bytes;
     float k;
     unsigned int* status;
 };
 
+// Slot layout: group record (A images, source coordinates), the unit's targets,
+// B hi and lo (2T rows each, T <= tg), metadata.
+__host__ __device__ inline int slot_t_off(int rb_count) { return record_bytes(rb_count); }
+__host__ __device__ inline int slot_b_off(int rb_count, int tg) { return record_bytes(rb_count) + tg * 16; }
+__host__ __device__ inline int slot_b_half(int tg) { return (2 * tg / 8) * kSbo; }
+__host__ __device__ inline int slot_meta_off(int rb_count, int tg) { return slot_b_off(rb_count, tg) + 2 * slot_b_half(tg); }
+__host__ __device__ inline int slot_bytes_for(int rb_count, int tg) {
+    return (slot_meta_off(rb_count, tg) + 16 + 1023) / 1024 * 1024;
+}
+constexpr int kEpiBytes = 8 * 64 * 8;  // epilogue exchange: 8 targets x 64 RHS x complex
+__host__ __device__ inline int tc_smem_bytes(int slots, int slot_bytes) {
+    return kSets * slots * slot_bytes + kEpiBytes + 1024;
+}
+
+// Metadata of a stage (int4): x = group (-1: padding, nothing to do), y = flags,
+// z = targets of the unit.  Flags: first quad of the unit (the stage carries the
+// unit's targets, the set's accumulator starts), last quad, done.
+constexpr int kFirst = 1, kLast = 2, kDone = 4;
+
 struct TcSmem {
-    unsigned char* stage[2];
-    float4* tx;
-    float4* sx;
-    int* sj;
-    int* seg;
-    uint64_t* bars;
+    unsigned char* slots;  // kSets x slots
+    float2* epi;
+    uint64_t* full;        // [kSets * slots] TMA bytes + producer arrival
+    uint64_t* empty;       // [kSets * slots] MMA commit
+    uint64_t* acc_full;    // [2] one commit per set after a unit's last quad
+    uint64_t* acc_empty;   // [2] the epilogue's 128 threads
     uint32_t* tmem_slot;
-    int* flag;
+    int* abort;
 };
 
-__device__ __forceinline__ TcSmem carve(unsigned char* smem, int np) {
+__device__ __forceinline__ TcSmem carve(unsigned char* smem, int slots, int slot_bytes) {
     TcSmem s;
-    const int sb = stage_bytes(np);
-    s.stage[0] = smem;
-    s.stage[1] = smem + sb;
-    unsigned char* e = smem + 2 * sb;
-    s.tx = reinterpret_cast<float4*>(e);
-    s.sx = s.tx + 64;
-    s.sj = reinterpret_cast<int*>(s.sx + 32);
-    s.seg = s.sj + 32;
-    s.bars = reinterpret_cast<uint64_t*>(s.seg + 64);
-    s.tmem_slot = reinterpret_cast<uint32_t*>(s.bars + 2);
-    s.flag = reinterpret_cast<int*>(s.tmem_slot + 1);
+    const int n = kSets * slots;
+    s.slots = smem;
+    s.epi = reinterpret_cast<float2*>(smem + (size_t)n * slot_bytes);
+    uint64_t* b = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(s.epi) + kEpiBytes);
+    s.full = b;
+    s.empty = b + n;
+    s.acc_full = b + 2 * n;
+    s.acc_empty = b + 2 * n + 2;
+    s.tmem_slot = reinterpret_cast<uint32_t*>(b + 2 * n + 4);
+    s.abort = reinterpret_cast<int*>(s.tmem_slot + 1);
     return s;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_p2p_tc(const TcArgs a) {
+__device__ __forceinline__ void set_abort(const TcArgs& a, const TcSmem& sm) {
+    *(volatile int*)sm.abort = 1;
+    atomicOr(a.status, P2P_DEV_TIMEOUT | P2P_DEV_TC_FAULTED);
+}
+
+// Unit u of the round-robin sequence: target box, first target, target count (0: empty unit).
+__device__ __forceinline__ void unit_of(const TcArgs& a, int64_t u, int& b, int& t0, int& nt) {
+    b = (int)(u / a.ngrp);
+    t0 = (int)(u - (int64_t)b * a.ngrp) * a.tg;
+    const int n_b = a.box_ptr[b + 1] - a.box_ptr[b];
+    nt = max(0, min(a.tg, n_b - t0));
+}
+
+// Ring of one set's slots: slot index and the parity of its round.
+struct Ring {
+    int slot;
+    uint32_t phase;
+    __device__ __forceinline__ void advance(int slots) {
+        if (++slot == slots) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
+// ---- producer (warp 0; lane s < kSets feeds set s) ----
+// A unit's group list is walked four entries (a quad) at a time, entry 4q + s going to set s.
+__device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, int lane) {
+    volatile int* abort = sm.abort;
+    const bool active = lane < kSets;
+    const int set = active ? lane : 0;
+    Ring r{0, 0u};
+    const uint32_t rec = (uint32_t)record_bytes(a.rb_count);
+    const int t_off = slot_t_off(a.rb_count), meta_off = slot_meta_off(a.rb_count, a.tg);
+    bool failed = false;
+    auto slot_base = [&](int slot) { return sm.slots + (size_t)(set * a.slots + slot) * a.slot_bytes; };
+    for (int64_t u = blockIdx.x; u < units && !failed; u += gridDim.x) {
+        int b, t0, nt;
+        unit_of(a, u, b, t0, nt);
+        if (nt == 0) continue;
+        const int off = a.glist_off[b], len = a.glist_off[b + 1] - off;
+        const float4* tsrc = a.xs + a.box_ptr[b] + t0;
+        for (int w0 = 0; w0 < len && !failed; w0 += 32) {
+            // 32 entries of the list (8 quads) in the warp's lanes
+            const int gl = w0 + lane < len ? a.glist[off + w0 + lane] : -1;
+            const int nq = min(8, (len - w0) / kSets);
+            for (int q = 0; q < nq; ++q) {
+                const int g = __shfl_sync(P2P_FULL_MASK, gl, q * kSets + set);
+                bool ok = true;
+                if (active) ok = mbar_wait(&sm.empty[set * a.slots + r.slot], r.phase ^ 1u, abort);
+                if (!__all_sync(P2P_FULL_MASK, ok)) {
+                    if (!ok && !*abort) set_abort(a, sm);
+                    failed = true;
+                    break;
+                }
+                if (active) {
+                    unsigned char* base = slot_base(r.slot);
+                    const int qq = (w0 >> 2) + q;
+                    const bool first = qq == 0, last = w0 + (q + 1) * kSets == len;
+                    *reinterpret_cast<int4*>(base + meta_off) =
+                        make_int4(g, (first ? kFirst : 0) | (last ? kLast : 0), nt, 0);
+                    uint64_t* bar = &sm.full[set * a.slots + r.slot];
+                    if (g >= 0) {
+                        fence_async_smem();  // the slot was last read through the generic proxy
+                        mbar_expect_tx(bar, rec + (first ? (uint32_t)nt * 16u : 0u));
+                        bulk_g2s(base, a.pack + (int64_t)g * rec, rec, bar);
+                        if (first) bulk_g2s(base + t_off, tsrc, (uint32_t)nt * 16u, bar);
+                    } else {
+                        mbar_arrive(bar);
+                    }
+                }
+                r.advance(a.slots);
+            }
+        }
+    }
+    // a terminal stage for each set
+    if (!failed) {
+        bool ok = true;
+        if (active) ok = mbar_wait(&sm.empty[set * a.slots + r.slot], r.phase ^ 1u, abort);
+        if (__all_sync(P2P_FULL_MASK, ok)) {
+            if (active) {
+                *reinterpret_cast<int4*>(slot_base(r.slot) + meta_off) = make_int4(-1, kDone, 0, 0);
+                mbar_arrive(&sm.full[set * a.slots + r.slot]);
+            }
+        } else {
+            if (!ok && !*abort) set_abort(a, sm);
+            failed = true;
+        }
+    }
+    if (failed && active) {
+        // wait (bounded) for the bulk copies of this set's latest round of slots
+        for (int i = 0; i < a.slots; ++i) {
+            if (--r.slot < 0) {
+                r.slot += a.slots;
+                r.phase ^= 1u;
+            }
+            mbar_wait(&sm.full[set * a.slots + r.slot], r.phase, nullptr, kDrainLimit);
+        }
+    }
+}
+
+// ---- G sets (128 threads each); the set's first thread issues its MMAs ----
+template <int KERN, int SP>
+__device__ __forceinline__ void g_tile(const float4* __restrict__ sx, float4 tx, int t, int h, int T,
+                                       unsigned char* b_hi, unsigned char* b_lo, float k) {
+    float re[SP], im[SP];
+#pragma unroll
+    for (int e = 0; e < SP; ++e) {
+        const float4 p = sx[h * SP + e];
+        const float dx = p.x - tx.x, dy = p.y - tx.y, dz = p.z - tx.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float inv = rsqrtf(r2);
+        const bool ok = r2 > 0.f && p.w == 0.f;  // r = 0 skipped; padding slots give 0
+        if (KERN == P2P_LAPLACE) {
+            re[e] = ok ? inv : 0.f;
+            im[e] = 0.f;
+        } else {
+            float sn, cs;
+            __sincosf(k * (r2 * inv), &sn, &cs);
+            re[e] = ok ? cs * inv : 0.f;
+            im[e] = ok ? sn * inv : 0.f;
+        }
+    }
+    store_split<SP>(b_hi, b_lo, op_off(t, h * SP), re);
+    store_split<SP>(b_hi, b_lo, op_off(T + t, h * SP), im);
+}
+
+template <int KERN>
+__device__ void run_gset(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int set, int i) {
+    volatile int* abort = sm.abort;
+    const int t_off = slot_t_off(a.rb_count), b_off = slot_b_off(a.rb_count, a.tg);
+    const int b_half = slot_b_half(a.tg), meta_off = slot_meta_off(a.rb_count, a.tg);
+    const bool leader = i == 0;
+    const uint32_t acc_cols = (uint32_t)(a.rb_count * 2 * a.tg);
+    float4 tx = make_float4(0.f, 0.f, 0.f, 0.f);
+    Ring r{0, 0u};
+    uint32_t unit = 0;
+    bool acc_started = false;
+    while (true) {
+        const int idx = set * a.slots + r.slot;
+        unsigned char* base = sm.slots + (size_t)idx * a.slot_bytes;
+        const bool ok = mbar_wait(&sm.full[idx], r.phase, abort);
+        // the set's 128 threads decide together (they meet at a named barrier below)
+        int any_fail;
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\tsetp.eq.s32 q, %1, 0;\n\tbar.red.or.pred p, %2, 128, q;\n\tselp.s32 %0, 1, 0, p;\n\t}"
+            : "=r"(any_fail)
+            : "r"((int)ok), "r"(1 + set)
+            : "memory");
+        if (any_fail) {
+            if (!ok && !*abort) set_abort(a, sm);
+            break;
+        }
+        const int4 m = *reinterpret_cast<const int4*>(base + meta_off);
+        if (m.y & kDone) break;
+        const int T = (m.z + 7) & ~7;
+        if (m.x >= 0) {
+            // sources per task: the smallest power of two with 16 T / SP <= 128 tasks
+            const int sp = T <= 8 ? 1 : (T <= 16 ? 2 : (T <= 32 ? 4 : 8));
+            const int tasks = kSrcGroup * T / sp;
+            const int t = i % T, h = i / T;
+            const float4* sx = reinterpret_cast<const float4*>(base + kImage * a.rb_count);
+            if (m.y & kFirst) {
+                const float4* st = reinterpret_cast<const float4*>(base + t_off);
+                tx = t < m.z ? st[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (i < tasks) {
+                unsigned char* b_hi = base + b_off;
+                unsigned char* b_lo = b_hi + b_half;
+                if (sp == 8) g_tile<KERN, 8>(sx, tx, t, h, T, b_hi, b_lo, a.k);
+                else if (sp == 4) g_tile<KERN, 4>(sx, tx, t, h, T, b_hi, b_lo, a.k);
+                else if (sp == 2) g_tile<KERN, 2>(sx, tx, t, h, T, b_hi, b_lo, a.k);
+                else g_tile<KERN, 1>(sx, tx, t, h, T, b_hi, b_lo, a.k);
+            }
+            fence_async_smem();
+        }
+        asm volatile("bar.sync %0, 128;" ::"r"(1 + set) : "memory");
+        if (leader) {
+            const uint32_t ub = unit & 1u;
+            bool fine = true;
+            if (m.y & kFirst) {
+                // the epilogue has released this accumulator buffer (unit - 2)
+                fine = mbar_wait(&sm.acc_empty[ub], ((unit >> 1) & 1u) ^ 1u, abort);
+                acc_started = false;
+            }
+            if (fine) {
+                tc_fence_after();
+                if (m.x >= 0) {
+                    const uint32_t idesc = idesc_bf16_f32(2 * T);
+                    const uint32_t sbase = smem_u32(base);
+                    const uint64_t db_hi = smem_desc(sbase + (uint32_t)b_off);
+                    const uint64_t db_lo = db_hi + (uint64_t)(b_half >> 4);
+                    const uint32_t d0 = tmem + ub * kSetCols + (uint32_t)set * acc_cols;
+                    for (int rb = 0; rb < a.rb_count; ++rb) {
+                        const uint64_t da_hi = smem_desc(sbase + (uint32_t)rb * kImage);
+                        const uint64_t da_lo = da_hi + (uint64_t)((kImage / 2) >> 4);
+                        const uint32_t d = d0 + (uint32_t)(rb * 2 * a.tg);
+                        mma_bf16(d, da_hi, db_hi, idesc, acc_started ? 1u : 0u);
+                        mma_bf16(d, da_hi, db_lo, idesc, 1u);
+                        mma_bf16(d, da_lo, db_hi, idesc, 1u);
+                    }
+                    acc_started = true;
+                }
+                mma_commit(&sm.empty[idx]);
+                if (m.y & kLast) mma_commit(&sm.acc_full[ub]);
+            } else if (!*abort) {
+                set_abort(a, sm);
+            }
+        }
+        if (m.y & kLast) ++unit;
+        r.advance(a.slots);
+    }
+    if (leader && *abort) {
+        // the latest commits arrive once every MMA issued before them has completed
+        for (int j = 0; j < a.slots; ++j) {
+            if (--r.slot < 0) {
+                r.slot += a.slots;
+                r.phase ^= 1u;
+            }
+            mbar_wait(&sm.empty[set * a.slots + r.slot], r.phase, nullptr, kDrainLimit);
+        }
+    }
+}
+
+// ---- epilogue (128 threads, TMEM lanes by warp quadrant) ----
+__device__ void run_epilogue(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int64_t units, int warp, int lane) {
+    volatile int* abort = sm.abort;
+    const int q = warp & 3;
+    const int m = q * 32 + lane;  // accumulator row
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    const uint32_t acc_cols = (uint32_t)(a.rb_count * 2 * a.tg);
+    uint32_t k = 0;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        int b, t0, nt;
+        unit_of(a, u, b, t0, nt);
+        if (nt == 0) continue;
+        // sets with work in this unit: entries 0 .. gcount - 1 of the list go to sets 0, 1, 2, 3, 0, ...
+        const int used = min(kSets, a.gcount[b]);
+        const int T = (nt + 7) & ~7;
+        const int tb = a.box_ptr[b] + t0;
+        const uint32_t ub = k & 1u, par = (k >> 1) & 1u;
+        ++k;
+        const bool ok = mbar_wait(&sm.acc_full[ub], par, abort);
+        // the 128 threads leave together (they meet at named barriers below)
+        if (epi_any(!ok)) {
+            if (!ok && !*abort) set_abort(a, sm);
+            return;
+        }
+        tc_fence_after();
+        for (int rb = 0; rb < a.rb_count; ++rb) {
+            const int r = rb * 64 + (m & 63);
+            for (int c0 = 0; c0 < T; c0 += 8) {
+                __syncwarp();
+                int prow[8];
+                if (m < 64) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) prow[j] = c0 + j < nt ? a.perm[tb + c0 + j] : 0;
+                }
+                const uint32_t col = lane_addr + ub * kSetCols + (uint32_t)(rb * 2 * a.tg + c0);
+                float x[8], y[8];
+                tmem_ld8(col, x);
+                tmem_ld8(col + (uint32_t)T, y);
+                for (int s = 1; s < used; ++s) {
+                    float x1[8], y1[8];
+                    tmem_ld8(col + (uint32_t)s * acc_cols, x1);
+                    tmem_ld8(col + (uint32_t)s * acc_cols + (uint32_t)T, y1);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        x[j] += x1[j];
+                        y[j] += y1[j];
+                    }
+                }
+                // rows 64..127 (Im lambda) hand (-D[., T + t], D[., t]) to rows 0..63
+                if (m >= 64) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) sm.epi[j * 64 + (m - 64)] = make_float2(-y[j], x[j]);
+                }
+                epi_sync();
+                if (m < 64 && r < a.nrhs) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (c0 + j < nt) {
+                            const float2 w = sm.epi[j * 64 + m];
+                            a.out[(int64_t)prow[j] * a.ld + r] =
+                                make_float2((x[j] + w.x) * kInv4Pi, (y[j] + w.y) * kInv4Pi);
+                        }
+                    }
+                }
+                epi_sync();
+            }
+        }
+        tc_fence_before();
+        mbar_arrive(&sm.acc_empty[ub]);
+    }
+}
+
+template <int KERN>
+__global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int b = blockIdx.x;
-    const int tb = a.box_ptr[b];
-    const int nt_all = a.box_ptr[b + 1] - tb;
-    const int t0 = blockIdx.y * kTcTargets;
-    if (t0 >= nt_all) return;  // uniform over the CTA
-    const int nt = min(kTcTargets, nt_all - t0);
-    const int S = a.box_src[b];
-    const int nstages = (S + kTcStageSrc - 1) / kTcStageSrc;
-    const int np = a.np;
-    TcSmem sm = carve(smem, np);
-    const int e0 = a.nbr_ptr[b];
-    const int ne = a.nbr_ptr[b + 1] - e0;
-
-    if (warp == 0) tmem_alloc(sm.tmem_slot, (uint32_t)a.tmem_cols);
-    if (tid == 0) {
-        mbar_init(&sm.bars[0], 1);
-        mbar_init(&sm.bars[1], 1);
+    const TcSmem sm = carve(smem, a.slots, a.slot_bytes);
+    if (warp == 0) tmem_alloc(sm.tmem_slot, 512u);
+    if (tid == 32) {
+        for (int i = 0; i < kSets * a.slots; ++i) {
+            mbar_init(&sm.full[i], 1);
+            mbar_init(&sm.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.acc_full[i], kSets);
+            mbar_init(&sm.acc_empty[i], 128);
+        }
+        *sm.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *sm.flag = 0;
     }
-    if (warp == 1) {
-        int start = 0, len = 0;
-        if (lane < ne) {
-            const int c = a.nbr_idx[e0 + lane];
-            start = a.box_ptr[c];
-            len = a.box_ptr[c + 1] - start;
-        }
-        int incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(P2P_FULL_MASK, incl, o);
-            if (lane >= o) incl += y;
-        }
-        sm.seg[lane] = incl - len;
-        sm.seg[32 + lane] = start;
-    }
-    if (tid < kTcTargets) sm.tx[tid] = tid < nt ? a.xs[tb + t0 + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *sm.tmem_slot;
-    const uint32_t idesc = idesc_bf16_f32(np);
-    const float k = a.k;
-
-    bool failed = false;
-    int committed = 0;  // stages whose MMAs were issued and committed
-    for (int st = 0; st < nstages; ++st) {
-        const int bi = st & 1;
-        unsigned char* A_hi = sm.stage[bi];
-        unsigned char* A_lo = A_hi + kATile;
-        unsigned char* B_hi = A_lo + kATile;
-        unsigned char* B_lo = B_hi + b_tile_bytes(np);
-        if (st >= 2 && !mbar_wait(&sm.bars[bi], (uint32_t)(((st >> 1) - 1) & 1))) *sm.flag = 1;
-        const int p0 = st * kTcStageSrc;
-        const int ns = min(kTcStageSrc, S - p0);
-        if (tid < kTcStageSrc) {
-            if (tid < ns) {
-                const int pp = p0 + tid;
-                int lo = 0, hi = ne - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (sm.seg[mid] <= pp) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int j = sm.seg[32 + lo] + (pp - sm.seg[lo]);
-                sm.sj[tid] = j;
-                sm.sx[tid] = a.xs[j];
-            } else {
-                sm.sj[tid] = -1;
-                sm.sx[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-        __syncthreads();
-        if (*sm.flag) {
-            failed = true;
-            break;
-        }
-        // B: warp w fills source quads w and w + 4; lanes run over right-hand sides
-#pragma unroll
-        for (int qi = 0; qi < 2; ++qi) {
-            const int kc = warp + 4 * qi;
-            int js[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) js[u] = sm.sj[4 * kc + u];
-            for (int r = lane; r < np; r += 32) {
-                float v[8];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    float2 l = make_float2(0.f, 0.f);
-                    if (js[u] >= 0 && r < a.nrhs) l = a.lam[(int64_t)js[u] * a.nrhs + r];
-                    v[2 * u] = l.x;
-                    v[2 * u + 1] = l.y;
-                }
-                store_split8(B_hi, B_lo, core_off(r, kc), v);
-            }
-        }
-        // A: thread -> target t, half of the stage's sources (4 quads)
-        {
-            const int t = tid & 63, half = tid >> 6;
-            const float4 x = sm.tx[t];
-            const bool tvalid = t < nt;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int kc = 4 * half + q;
-                float re_row[8], im_row[8];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int s = 4 * kc + u;
-                    const float4 p = sm.sx[s];
-                    const float dx = p.x - x.x, dy = p.y - x.y, dz = p.z - x.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float inv = rsqrtf(r2);
-                    inv = (r2 > 0.f && tvalid && s < ns) ? inv : 0.f;
-                    float gr, gi;
-                    if (a.laplace) {
-                        gr = inv;
-                        gi = 0.f;
-                    } else {
-                        float sn, cs;
-                        __sincosf(k * (r2 * inv), &sn, &cs);
-                        gr = cs * inv;
-                        gi = sn * inv;
-                    }
-                    re_row[2 * u] = gr;
-                    re_row[2 * u + 1] = -gi;
-                    im_row[2 * u] = gi;
-                    im_row[2 * u + 1] = gr;
-                }
-                const int off = core_off(2 * t, kc);
-                store_split8(A_hi, A_lo, off, re_row);
-                store_split8(A_hi, A_lo, off + 16, im_row);
-            }
-        }
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            // stage st accumulates into accumulator st % nacc: shorter accumulation chains
-            const uint32_t acc = tmem + (uint32_t)((st % a.nacc) * np);
-            issue_stage(acc, smem_u32(A_hi), smem_u32(A_lo), smem_u32(B_hi), smem_u32(B_lo), idesc, st < a.nacc);
-            mma_commit(&sm.bars[bi]);
-        }
-        committed = st + 1;
-    }
-
-    // wait for the last stage (all earlier MMAs complete before it)
-    if (!failed && nstages > 0) {
-        const int last = nstages - 1;
-        if (!mbar_wait(&sm.bars[last & 1], (uint32_t)((last >> 1) & 1))) *sm.flag = 1;
-    }
-    __syncthreads();
-    failed = failed || (*sm.flag != 0);
-    if (failed) {
-        if (tid == 0) atomicOr(a.status, P2P_DEV_TIMEOUT | P2P_DEV_TC_FAULTED);
-        // drain: bounded waits for the last committed stage of each barrier
-        if (tid == 0) {
-            for (int st = committed - 2; st < committed; ++st)
-                if (st >= 0) mbar_wait(&sm.bars[st & 1], (uint32_t)((st >> 1) & 1));
-        }
+    const int64_t units = (int64_t)a.nb * a.ngrp;
+    if (warp == 0) {
+        run_producer(a, sm, units, lane);
+    } else if (warp < kEpiWarp0) {
+        const int gw = warp - kGWarp0;
+        run_gset<KERN>(a, sm, tmem, gw >> 2, (gw & 3) * 32 + lane);
     } else {
-        tc_fence_after();
-        const int m = warp * 32 + lane;  // accumulator row of this lane
-        const int t = m >> 1;
-        const bool odd = (m & 1) != 0;
-        const bool write = t < nt;
-        const int64_t row = write ? (int64_t)a.perm[tb + t0 + t] * a.ld : 0;
-        const int used = min(a.nacc, nstages);
-        for (int c0 = 0; c0 < np; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            for (int q = 1; q < used; ++q) {
-                float w[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * np + c0), w);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += w[i];
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float x = __shfl_xor_sync(P2P_FULL_MASK, odd ? v[i] : v[8 + i], 1);
-                const int r = c0 + (odd ? 8 : 0) + i;
-                if (write && r < a.nrhs) {
-                    const float2 o = odd ? make_float2(x * kInv4Pi, v[8 + i] * kInv4Pi)
-                                         : make_float2(v[i] * kInv4Pi, x * kInv4Pi);
-                    a.out[row + r] = o;
-                }
-            }
-        }
+        run_epilogue(a, sm, tmem, units, warp, lane);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 512u);
+    }
 }
 
 // ------------------------------------------------- operand-layout self-check --
 
 // D[128 x N] = A[128 x K] . B[N x K]^T with A, B split into BF16 hi + lo (3 MMAs
-// per K = 16 slice), through the same descriptors and stage layout as k_p2p_tc.
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm_check(const float* __restrict__ A,
-                                                                 const float* __restrict__ B, float* __restrict__ D,
-                                                                 int K, int np, int tmem_cols,
-                                                                 unsigned int* __restrict__ status) {
+// per 16-wide K slice), through the same operand layout, descriptors and
+// instruction descriptor as k_p2p_tc.
+__global__ void __launch_bounds__(128, 1) k_tc_gemm_check(const float* __restrict__ A, const float* __restrict__ B,
+                                                          float* __restrict__ D, int K, int n, int tmem_cols,
+                                                          unsigned int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    TcSmem sm = carve(smem, np);
-    if (warp == 0) tmem_alloc(sm.tmem_slot, (uint32_t)tmem_cols);
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = a_hi + kImage / 2;
+    unsigned char* b_hi = smem + kImage;
+    unsigned char* b_lo = b_hi + (n / 8) * kSbo;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(b_lo + (n / 8) * kSbo);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+    if (warp == 0) tmem_alloc(slot, (uint32_t)tmem_cols);
     if (tid == 0) {
-        mbar_init(&sm.bars[0], 1);
-        mbar_init(&sm.bars[1], 1);
+        mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *sm.tmem_slot;
-    const uint32_t idesc = idesc_bf16_f32(np);
-    const int nstages = K / 64;
+    const uint32_t tmem = *slot;
+    const uint32_t idesc = idesc_bf16_f32(n);
     bool ok = true;
-    int committed = 0;
-    for (int st = 0; st < nstages && ok; ++st) {
-        const int bi = st & 1;
-        unsigned char* A_hi = sm.stage[bi];
-        unsigned char* A_lo = A_hi + kATile;
-        unsigned char* B_hi = A_lo + kATile;
-        unsigned char* B_lo = B_hi + b_tile_bytes(np);
-        if (st >= 2) ok = mbar_wait(&sm.bars[bi], (uint32_t)(((st >> 1) - 1) & 1));
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        for (int c = tid; c < 128 * 8; c += kTcThreads) {
-            const int row = c >> 3, kc = c & 7;
+    for (int ks = 0; ks < K / kSrcGroup && ok; ++ks) {
+        for (int c = tid; c < 128 * 2; c += 128) {
+            const int row = c >> 1, half = c & 1;
             float v[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = A[(int64_t)row * K + st * 64 + kc * 8 + i];
-            store_split8(A_hi, A_lo, core_off(row, kc), v);
+            for (int i = 0; i < 8; ++i) v[i] = A[(int64_t)row * K + ks * 16 + half * 8 + i];
+            store_split<8>(a_hi, a_lo, op_off(row, half * 8), v);
         }
-        for (int c = tid; c < np * 8; c += kTcThreads) {
-            const int row = c >> 3, kc = c & 7;
+        for (int c = tid; c < n * 2; c += 128) {
+            const int row = c >> 1, half = c & 1;
             float v[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = B[(int64_t)row * K + st * 64 + kc * 8 + i];
-            store_split8(B_hi, B_lo, core_off(row, kc), v);
+            for (int i = 0; i < 8; ++i) v[i] = B[(int64_t)row * K + ks * 16 + half * 8 + i];
+            store_split<8>(b_hi, b_lo, op_off(row, half * 8), v);
         }
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_stage(tmem, smem_u32(A_hi), smem_u32(A_lo), smem_u32(B_hi), smem_u32(B_lo), idesc, st == 0);
-            mma_commit(&sm.bars[bi]);
+            mma_bf16(tmem, smem_desc(smem_u32(a_hi)), smem_desc(smem_u32(b_hi)), idesc, ks == 0 ? 0u : 1u);
+            mma_bf16(tmem, smem_desc(smem_u32(a_hi)), smem_desc(smem_u32(b_lo)), idesc, 1u);
+            mma_bf16(tmem, smem_desc(smem_u32(a_lo)), smem_desc(smem_u32(b_hi)), idesc, 1u);
+            mma_commit(bar);
         }
-        committed = st + 1;
+        // the operands are rewritten next slice: wait for these MMAs
+        bool done = true;
+        if (tid == 0) done = mbar_wait(bar, (uint32_t)(ks & 1), nullptr);
+        ok = __syncthreads_and(done);
     }
-    if (ok && nstages > 0) ok = mbar_wait(&sm.bars[(nstages - 1) & 1], (uint32_t)(((nstages - 1) >> 1) & 1));
-    ok = __syncthreads_and(ok);
     if (ok) {
         tc_fence_after();
-        for (int c0 = 0; c0 < np; c0 += 16) {
+        for (int c0 = 0; c0 < n; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) D[(int64_t)(warp * 32 + lane) * np + c0 + i] = v[i];
+            for (int i = 0; i < 16; ++i) D[(int64_t)(warp * 32 + lane) * n + c0 + i] = v[i];
         }
     } else if (tid == 0) {
         atomicOr(status, P2P_DEV_TIMEOUT);
-        for (int st = committed - 2; st < committed; ++st)
-            if (st >= 0) mbar_wait(&sm.bars[st & 1], (uint32_t)((st >> 1) & 1));
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, (uint32_t)tmem_cols);
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, (uint32_t)tmem_cols);
+    }
 }
 
-int tmem_cols_for(int np) {
+int tmem_cols_for(int n) {
     int c = 32;
-    while (c < np) c <<= 1;
+    while (c < n) c <<= 1;
     return c;
+}
+
+// Launch shape for nrhs right-hand sides: RHS blocks, targets per unit, slots per set.
+struct TcShape {
+    int rb_count, tg, slots, slot_bytes, smem;
+};
+
+TcShape tc_shape(int32_t nrhs, int optin) {
+    TcShape s;
+    s.rb_count = (nrhs + 63) / 64;
+    // one accumulator per G set (rb_count blocks x 2T columns) in each of two unit buffers
+    s.tg = (kSetCols / (2 * kSets * s.rb_count)) / 8 * 8;
+    if (s.tg > 64) s.tg = 64;
+    s.slot_bytes = slot_bytes_for(s.rb_count, s.tg);
+    s.slots = 3;
+    while (s.slots > 1 && tc_smem_bytes(s.slots, s.slot_bytes) > optin) --s.slots;
+    s.smem = tc_smem_bytes(s.slots, s.slot_bytes);
+    // more than half an SM's shared memory keeps one CTA (and one 512-column TMEM allocation) per SM
+    const int half = 116 * 1024;
+    if (s.smem < half) s.smem = half;
+    return s;
 }
 
 }  // namespace
 
+size_t p2p_tc_pack_bytes(int64_t n, int32_t nb, int32_t max_nrhs) {
+    if (max_nrhs < 16) return 0;
+    const int64_t groups = n / kSrcGroup + nb;
+    return (size_t)groups * (size_t)record_bytes((max_nrhs + 63) / 64);
+}
+
 bool p2p_tc_supported(const p2p_plan* plan, int32_t nrhs) {
-    if (!plan || nrhs < 1 || nrhs > 256) return false;
+    if (!plan || !plan->tc_pack || nrhs < 1 || nrhs > 256 || nrhs > plan->max_nrhs) return false;
     int dev = 0, major = 0, minor = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
@@ -496,51 +817,66 @@ bool p2p_tc_supported(const p2p_plan* plan, int32_t nrhs) {
     return major == 10 && minor == 3;
 }
 
-p2p_status p2p_apply_tc(const p2p_plan* plan, const float2* lam_sorted, float2* out, int32_t nrhs, int64_t ld,
-                        int32_t adjoint, cudaStream_t s) {
+// Stage: the group records (strength images from original-order lambda via perm, coordinates).
+p2p_status p2p_tc_stage(const p2p_plan* plan, const float2* lam, int32_t nrhs, int64_t ld, cudaStream_t s) {
+    if (plan->n == 0 || plan->tc_groups == 0) return P2P_OK;
+    const int rb_count = (nrhs + 63) / 64;
+    dim3 grid((unsigned)plan->tc_groups, (unsigned)rb_count);
+    k_tc_pack<<<grid, 128, 0, s>>>(lam, ld, nrhs, plan->perm, plan->box_ptr, plan->xs, plan->tc_gstart, plan->nb,
+                                   rb_count, plan->tc_pack);
+    P2P_CHECK_LAUNCH("p2p_apply_stage/tc_pack");
+    return P2P_OK;
+}
+
+p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t ld, int32_t adjoint,
+                        cudaStream_t s) {
     if (plan->n == 0) return P2P_OK;
+    int dev = 0, optin = 0, sms = 0;
+    P2P_TRY_CUDA(cudaGetDevice(&dev), "p2p_apply_tc");
+    P2P_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "p2p_apply_tc");
+    P2P_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "p2p_apply_tc");
+    const TcShape sh = tc_shape(nrhs, optin);
+    if (sh.smem > optin) {
+        set_message("p2p_apply_tc: the tensor-core pipeline does not fit in shared memory");
+        return P2P_ERR_UNSUPPORTED;
+    }
     TcArgs a;
     a.xs = plan->xs;
-    a.lam = lam_sorted;
+    a.pack = plan->tc_pack;
     a.box_ptr = plan->box_ptr;
-    a.nbr_ptr = plan->nbr_ptr;
-    a.nbr_idx = plan->nbr_idx;
-    a.box_src = plan->box_src;
+    a.glist_off = plan->tc_glist_off;
+    a.glist = plan->tc_glist;
+    a.gcount = plan->tc_gcount;
     a.perm = plan->perm;
     a.out = out;
     a.ld = ld;
     a.nrhs = nrhs;
-    a.np = (nrhs + 15) / 16 * 16;
-    const int smem_needed = tc_smem_bytes(a.np);
-    int max_smem = 0, dev = 0;
-    P2P_TRY_CUDA(cudaGetDevice(&dev), "p2p_apply_tc");
-    P2P_TRY_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev), "p2p_apply_tc");
-    const int ctas_per_sm = max(1, max_smem / (smem_needed + 1024));
-    // up to four accumulators while the co-resident CTAs' TMEM fits in 512 columns
-    a.nacc = 4;
-    while (a.nacc > 1 && ctas_per_sm * tmem_cols_for(a.nacc * a.np) > 512) a.nacc >>= 1;
-    a.tmem_cols = tmem_cols_for(a.nacc * a.np);
-    a.laplace = plan->kernel == P2P_LAPLACE;
+    a.rb_count = sh.rb_count;
+    a.tg = sh.tg;
+    a.ngrp = (plan->max_box + sh.tg - 1) / sh.tg;
+    a.nb = plan->nb;
+    a.slots = sh.slots;
+    a.slot_bytes = sh.slot_bytes;
     a.k = adjoint ? -plan->k : plan->k;
     a.status = plan->status;
-    const int smem = smem_needed;
-    P2P_TRY_CUDA(cudaFuncSetAttribute(k_p2p_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "p2p_apply_tc");
-    const int groups = (plan->max_box + kTcTargets - 1) / kTcTargets;
-    dim3 grid((unsigned)plan->nb, (unsigned)groups);
-    k_p2p_tc<<<grid, kTcThreads, smem, s>>>(a);
+    auto kern = plan->kernel == P2P_LAPLACE ? k_p2p_tc<P2P_LAPLACE> : k_p2p_tc<P2P_HELMHOLTZ>;
+    P2P_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem), "p2p_apply_tc");
+    const int64_t units = (int64_t)a.nb * a.ngrp;
+    const int grid = (int)std::min<int64_t>(units, sms);
+    kern<<<grid, kThreads, sh.smem, s>>>(a);
     P2P_CHECK_LAUNCH("p2p_apply_tc");
     return P2P_OK;
 }
 
 extern "C" P2P_API p2p_status p2p_diag_tc_gemm(const float* A, const float* B, float* D, int32_t K, int32_t n,
                                                unsigned int* status, p2p_stream_t stream) {
-    if (!A || !B || !D || !status || K < 64 || K % 64 != 0 || n < 16 || n > 256 || n % 16 != 0)
+    if (!A || !B || !D || !status || K < 16 || K % 16 != 0 || n < 16 || n > 256 || n % 16 != 0)
         return P2P_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
-    const int smem = tc_smem_bytes(n);
+    const int smem = kImage + 2 * (n / 8) * kSbo + 64;
     P2P_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm_check, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                  "p2p_diag_tc_gemm");
-    k_tc_gemm_check<<<1, kTcThreads, smem, s>>>(A, B, D, K, n, tmem_cols_for(n), status);
+    k_tc_gemm_check<<<1, 128, smem, s>>>(A, B, D, K, n, tmem_cols_for(n), status);
     P2P_CHECK_LAUNCH("p2p_diag_tc_gemm");
     return P2P_OK;
 }

@@ -69,6 +69,21 @@ def test_tc_apply_parity(nrhs, kernel):
     assert err.max() <= TOL, err
 
 
+@pytest.mark.parametrize("nrhs", [96, 200])
+def test_tc_several_rhs_blocks(nrhs):
+    """More than 64 right-hand sides: several RHS blocks share each G tile."""
+    api = _api()
+    wl = _sphere(12000, 20, 37)
+    lam = W.strengths(wl.n, nrhs, 37)
+    plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, wl.k, max_nrhs=nrhs)
+    out = plan.apply(torch.from_numpy(lam).cuda(), path="tc_bf16x3").cpu().numpy()
+    assert plan.async_status() == 0
+    ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
+    err = rel_l2(out, ref)
+    print(f"nrhs={nrhs} tensor-core rel-L2 max {err.max():.3e}")
+    assert err.max() <= TOL, err
+
+
 def test_tc_dense_boxes_and_adjoint():
     """Boxes with more than 64 targets take several target groups."""
     api = _api()
