@@ -28,20 +28,19 @@
 //   warp 0       producer: walks a unit's group list four entries at a time; lane s issues entry 4q + s
 //                into a slot of G set s (metadata, TMA bulk copy of the record, the unit's targets with
 //                the first quad)
-//   warps 1-16   four G sets of four warps: G tile in FP32, BF16 hi/lo split into the slot's B operand;
-//                after a set-wide named barrier the set's first thread issues the three MMAs (per RHS
-//                block) into the set's own accumulator and commits them to the slot's release barrier
-//   warps 17-20  epilogue: sums the sets' accumulators (TMEM -> registers), combines Re/Im through
+//   warps 1-16   four G sets of four warps: G tile in FP32, BF16 hi/lo split into the slot's B operand
+//   warps 17-20  one MMA issuer per set (one thread): once the set has written B, the three MMAs (per RHS
+//                block) into the set's own accumulator, committed to the slot's release barrier
+//   warps 21-24  epilogue: sums the sets' accumulators (TMEM -> registers), combines Re/Im through
 //                shared memory and writes out[perm[t]]
 // Four independent issue chains (one per set) keep the tensor core fed with the
 // small (N = 2T) MMAs; two TMEM buffers alternate between a CTA's units so the
 // epilogue of one unit overlaps the MMAs of the next.
 //
 // Every wait is bounded: a wait that runs out sets the plan's status word and an
-// abort flag; every role then stops (the warps of a set or of the epilogue decide
-// together through a barrier reduction), the producer waits (bounded) for the
-// bulk copies it issued, each set's issuing thread for its MMAs, and the CTA
-// frees its TMEM and returns.
+// abort flag; every role then stops (the epilogue warps decide together through
+// a barrier reduction), the producer waits (bounded) for the bulk copies it
+// issued, each MMA issuer for its MMAs, and the CTA frees its TMEM and returns.
 //
 // Operands use the canonical K-major layout without swizzle: 8-row x 16-byte
 // core matrices, the two K-adjacent cores of a 16-wide K slice 128 bytes apart
@@ -61,7 +60,7 @@ constexpr int kImage = 8192;           // hi + lo images of one 128 x 16 A opera
 constexpr int kLbo = 128, kSbo = 256;  // core-matrix strides (K direction, 8-row groups)
 constexpr int kSetCols = 256;          // TMEM columns of one unit buffer (an accumulator per G set)
 constexpr int kSets = 4;               // G sets of four warps; set s takes list entries s, s + kSets, ...
-constexpr int kGWarp0 = 1, kEpiWarp0 = kGWarp0 + 4 * kSets;
+constexpr int kGWarp0 = 1, kMmaWarp0 = kGWarp0 + 4 * kSets, kEpiWarp0 = kMmaWarp0 + kSets;
 constexpr int kWarps = kEpiWarp0 + 4;
 constexpr int kThreads = kWarps * 32;
 constexpr uint32_t kWaitLimit = 1u << 22;
@@ -152,7 +151,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// Named barriers: 1 .. 4 for the G sets, 5 for the epilogue warps (0 is __syncthreads).
+// Named barrier 5 for the epilogue warps (0 is __syncthreads).
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 5, 128;" ::: "memory"); }
 // Barrier of the 128 epilogue threads that also ORs a condition over them.
 __device__ __forceinline__ bool epi_any(bool c) {
@@ -327,7 +326,7 @@ __host__ __device__ inline int slot_bytes_for(int rb_count, int tg) {
 }
 constexpr int kEpiBytes = 8 * 64 * 8;  // epilogue exchange: 8 targets x 64 RHS x complex
 __host__ __device__ inline int tc_smem_bytes(int slots, int slot_bytes) {
-    return kSets * slots * slot_bytes + kEpiBytes + 1024;
+    return kSets * slots * slot_bytes + kEpiBytes + 1024;  // barriers: (3 kSets slots + 4) x 8 bytes <= 1024
 }
 
 // Metadata of a stage (int4): x = group (-1: padding, nothing to do), y = flags,
@@ -339,6 +338,7 @@ struct TcSmem {
     unsigned char* slots;  // kSets x slots
     float2* epi;
     uint64_t* full;        // [kSets * slots] TMA bytes + producer arrival
+    uint64_t* full_b;      // [kSets * slots] the G set's 128 threads (B operand written)
     uint64_t* empty;       // [kSets * slots] MMA commit
     uint64_t* acc_full;    // [2] one commit per set after a unit's last quad
     uint64_t* acc_empty;   // [2] the epilogue's 128 threads
@@ -353,10 +353,11 @@ __device__ __forceinline__ TcSmem carve(unsigned char* smem, int slots, int slot
     s.epi = reinterpret_cast<float2*>(smem + (size_t)n * slot_bytes);
     uint64_t* b = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(s.epi) + kEpiBytes);
     s.full = b;
-    s.empty = b + n;
-    s.acc_full = b + 2 * n;
-    s.acc_empty = b + 2 * n + 2;
-    s.tmem_slot = reinterpret_cast<uint32_t*>(b + 2 * n + 4);
+    s.full_b = b + n;
+    s.empty = b + 2 * n;
+    s.acc_full = b + 3 * n;
+    s.acc_empty = b + 3 * n + 2;
+    s.tmem_slot = reinterpret_cast<uint32_t*>(b + 3 * n + 4);
     s.abort = reinterpret_cast<int*>(s.tmem_slot + 1);
     return s;
 }
@@ -489,35 +490,23 @@ __device__ __forceinline__ void g_tile(const float4* __restrict__ sx, float4 tx,
 }
 
 template <int KERN>
-__device__ void run_gset(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int set, int i) {
+__device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
     volatile int* abort = sm.abort;
     const int t_off = slot_t_off(a.rb_count), b_off = slot_b_off(a.rb_count, a.tg);
     const int b_half = slot_b_half(a.tg), meta_off = slot_meta_off(a.rb_count, a.tg);
-    const bool leader = i == 0;
-    const uint32_t acc_cols = (uint32_t)(a.rb_count * 2 * a.tg);
     float4 tx = make_float4(0.f, 0.f, 0.f, 0.f);
     Ring r{0, 0u};
-    uint32_t unit = 0;
-    bool acc_started = false;
     while (true) {
         const int idx = set * a.slots + r.slot;
         unsigned char* base = sm.slots + (size_t)idx * a.slot_bytes;
-        const bool ok = mbar_wait(&sm.full[idx], r.phase, abort);
-        // the set's 128 threads decide together (they meet at a named barrier below)
-        int any_fail;
-        asm volatile(
-            "{\n\t.reg .pred p, q;\n\tsetp.eq.s32 q, %1, 0;\n\tbar.red.or.pred p, %2, 128, q;\n\tselp.s32 %0, 1, 0, p;\n\t}"
-            : "=r"(any_fail)
-            : "r"((int)ok), "r"(1 + set)
-            : "memory");
-        if (any_fail) {
-            if (!ok && !*abort) set_abort(a, sm);
+        if (!mbar_wait(&sm.full[idx], r.phase, abort)) {
+            if (!*abort) set_abort(a, sm);
             break;
         }
         const int4 m = *reinterpret_cast<const int4*>(base + meta_off);
         if (m.y & kDone) break;
-        const int T = (m.z + 7) & ~7;
         if (m.x >= 0) {
+            const int T = (m.z + 7) & ~7;
             // sources per task: the smallest power of two with 16 T / SP <= 128 tasks
             const int sp = T <= 8 ? 1 : (T <= 16 ? 2 : (T <= 32 ? 4 : 8));
             const int tasks = kSrcGroup * T / sp;
@@ -537,51 +526,75 @@ __device__ void run_gset(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int s
             }
             fence_async_smem();
         }
-        asm volatile("bar.sync %0, 128;" ::"r"(1 + set) : "memory");
-        if (leader) {
-            const uint32_t ub = unit & 1u;
-            bool fine = true;
-            if (m.y & kFirst) {
-                // the epilogue has released this accumulator buffer (unit - 2)
-                fine = mbar_wait(&sm.acc_empty[ub], ((unit >> 1) & 1u) ^ 1u, abort);
-                acc_started = false;
-            }
-            if (fine) {
-                tc_fence_after();
-                if (m.x >= 0) {
-                    const uint32_t idesc = idesc_bf16_f32(2 * T);
-                    const uint32_t sbase = smem_u32(base);
-                    const uint64_t db_hi = smem_desc(sbase + (uint32_t)b_off);
-                    const uint64_t db_lo = db_hi + (uint64_t)(b_half >> 4);
-                    const uint32_t d0 = tmem + ub * kSetCols + (uint32_t)set * acc_cols;
-                    for (int rb = 0; rb < a.rb_count; ++rb) {
-                        const uint64_t da_hi = smem_desc(sbase + (uint32_t)rb * kImage);
-                        const uint64_t da_lo = da_hi + (uint64_t)((kImage / 2) >> 4);
-                        const uint32_t d = d0 + (uint32_t)(rb * 2 * a.tg);
-                        mma_bf16(d, da_hi, db_hi, idesc, acc_started ? 1u : 0u);
-                        mma_bf16(d, da_hi, db_lo, idesc, 1u);
-                        mma_bf16(d, da_lo, db_hi, idesc, 1u);
-                    }
-                    acc_started = true;
-                }
-                mma_commit(&sm.empty[idx]);
-                if (m.y & kLast) mma_commit(&sm.acc_full[ub]);
-            } else if (!*abort) {
-                set_abort(a, sm);
-            }
-        }
-        if (m.y & kLast) ++unit;
+        mbar_arrive(&sm.full_b[idx]);
         r.advance(a.slots);
     }
-    if (leader && *abort) {
-        // the latest commits arrive once every MMA issued before them has completed
-        for (int j = 0; j < a.slots; ++j) {
-            if (--r.slot < 0) {
-                r.slot += a.slots;
-                r.phase ^= 1u;
-            }
-            mbar_wait(&sm.empty[set * a.slots + r.slot], r.phase, nullptr, kDrainLimit);
+}
+
+// ---- MMA issuer of a set (one thread) ----
+__device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int set) {
+    volatile int* abort = sm.abort;
+    const int b_off = slot_b_off(a.rb_count, a.tg), b_half = slot_b_half(a.tg);
+    const int meta_off = slot_meta_off(a.rb_count, a.tg);
+    const uint32_t acc_cols = (uint32_t)(a.rb_count * 2 * a.tg);
+    Ring r{0, 0u};
+    uint32_t unit = 0;
+    bool acc_started = false, issued = false;
+    while (true) {
+        const int idx = set * a.slots + r.slot;
+        unsigned char* base = sm.slots + (size_t)idx * a.slot_bytes;
+        if (!mbar_wait(&sm.full[idx], r.phase, abort)) {
+            if (!*abort) set_abort(a, sm);
+            break;
         }
+        const int4 m = *reinterpret_cast<const int4*>(base + meta_off);
+        if (m.y & kDone) break;
+        const uint32_t ub = unit & 1u;
+        if (m.y & kFirst) {
+            // the epilogue has released this accumulator buffer (unit - 2)
+            if (!mbar_wait(&sm.acc_empty[ub], ((unit >> 1) & 1u) ^ 1u, abort)) {
+                if (!*abort) set_abort(a, sm);
+                break;
+            }
+            acc_started = false;
+        }
+        if (!mbar_wait(&sm.full_b[idx], r.phase, abort)) {
+            if (!*abort) set_abort(a, sm);
+            break;
+        }
+        tc_fence_after();
+        if (m.x >= 0) {
+            const int T = (m.z + 7) & ~7;
+            const uint32_t idesc = idesc_bf16_f32(2 * T);
+            const uint32_t sbase = smem_u32(base);
+            const uint64_t db_hi = smem_desc(sbase + (uint32_t)b_off);
+            const uint64_t db_lo = db_hi + (uint64_t)(b_half >> 4);
+            const uint32_t d0 = tmem + ub * kSetCols + (uint32_t)set * acc_cols;
+            for (int rb = 0; rb < a.rb_count; ++rb) {
+                const uint64_t da_hi = smem_desc(sbase + (uint32_t)rb * kImage);
+                const uint64_t da_lo = da_hi + (uint64_t)((kImage / 2) >> 4);
+                const uint32_t d = d0 + (uint32_t)(rb * 2 * a.tg);
+                mma_bf16(d, da_hi, db_hi, idesc, acc_started ? 1u : 0u);
+                mma_bf16(d, da_hi, db_lo, idesc, 1u);
+                mma_bf16(d, da_lo, db_hi, idesc, 1u);
+            }
+            acc_started = true;
+        }
+        mma_commit(&sm.empty[idx]);
+        issued = true;
+        if (m.y & kLast) {
+            mma_commit(&sm.acc_full[ub]);
+            ++unit;
+        }
+        r.advance(a.slots);
+    }
+    if (*abort && issued) {
+        // the latest commit arrives once every MMA issued before it has completed
+        if (--r.slot < 0) {
+            r.slot += a.slots;
+            r.phase ^= 1u;
+        }
+        mbar_wait(&sm.empty[set * a.slots + r.slot], r.phase, nullptr, kDrainLimit);
     }
 }
 
@@ -666,6 +679,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ 
     if (tid == 32) {
         for (int i = 0; i < kSets * a.slots; ++i) {
             mbar_init(&sm.full[i], 1);
+            mbar_init(&sm.full_b[i], 128);
             mbar_init(&sm.empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -682,9 +696,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ 
     const int64_t units = (int64_t)a.nb * a.ngrp;
     if (warp == 0) {
         run_producer(a, sm, units, lane);
-    } else if (warp < kEpiWarp0) {
+    } else if (warp < kMmaWarp0) {
         const int gw = warp - kGWarp0;
-        run_gset<KERN>(a, sm, tmem, gw >> 2, (gw & 3) * 32 + lane);
+        run_gset<KERN>(a, sm, gw >> 2, (gw & 3) * 32 + lane);
+    } else if (warp < kEpiWarp0) {
+        if (lane == 0) run_mma(a, sm, tmem, warp - kMmaWarp0);
     } else {
         run_epilogue(a, sm, tmem, units, warp, lane);
     }
