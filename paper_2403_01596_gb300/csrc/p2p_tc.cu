@@ -807,7 +807,7 @@ TcShape tc_shape(int32_t nrhs, int optin) {
     s.tg = (kSetCols / (2 * kSets * s.rb_count)) / 8 * 8;
     if (s.tg > 64) s.tg = 64;
     s.slot_bytes = slot_bytes_for(s.rb_count, s.tg);
-    s.slots = 3;
+    s.slots = 4;
     while (s.slots > 1 && tc_smem_bytes(s.slots, s.slot_bytes) > optin) --s.slots;
     s.smem = tc_smem_bytes(s.slots, s.slot_bytes);
     // more than half an SM's shared memory keeps one CTA (and one 512-column TMEM allocation) per SM
