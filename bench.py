@@ -259,7 +259,7 @@ def _traffic_for(kernel_src_hash: str, layout: str):
 
 def _kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("p2p_apply.cu", "p2p_internal.cuh"):
+    for f in ("p2p_apply.cu", "p2p_pair.cuh", "p2p_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2403_01596_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -520,7 +520,8 @@ def run_multirhs(args):
     t_tc = kern_ms * 1e-3                                                 # the pipelined kernel alone
     sizes = torch.diff(plan.structure.box_ptr.long())
     groups = int(((sizes + 15) // 16).sum().item())                      # 16-source groups of the pre-pack
-    pack_bytes = wl.n * nrhs * 8 + groups * 8192 * ((nrhs + 63) // 64)   # strengths read, images written
+    record = ((nrhs + 63) // 64) * 8192 + 16 * 16                        # BF16 hi/lo images + coordinates
+    pack_bytes = wl.n * (nrhs * 8 + 16) + groups * record                 # strengths, coordinates read; records written
     line = {"metric": METRIC + " [64-RHS: pair x RHS]", "value": res["tc_bf16x3"]["gpair_rhs_s"], "unit": UNIT,
             "n_gpus": 1, "steps": args.ext_steps, "warmup": 2, "ms_per_step": res["tc_bf16x3"]["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/f32",

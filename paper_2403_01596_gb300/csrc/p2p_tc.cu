@@ -63,8 +63,12 @@ constexpr int kSets = 4;               // G sets of four warps; set s takes list
 constexpr int kGWarp0 = 1, kMmaWarp0 = kGWarp0 + 4 * kSets, kEpiWarp0 = kMmaWarp0 + kSets;
 constexpr int kWarps = kEpiWarp0 + 4;
 constexpr int kThreads = kWarps * 32;
-constexpr uint32_t kWaitLimit = 1u << 22;
-constexpr uint32_t kDrainLimit = 1u << 16;
+// A waiting thread is suspended (up to kSuspendNs per poll) until the phase
+// completes, so idle roles do not take issue slots from the working warps.
+// kWaitLimit polls bound every wait to a few seconds at most.
+constexpr uint32_t kSuspendNs = 10000;
+constexpr uint32_t kWaitLimit = 1u << 18;
+constexpr uint32_t kDrainLimit = 1u << 14;
 
 // --------------------------------------------------------------- PTX helpers --
 
@@ -90,10 +94,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return done != 0;
 }
@@ -103,7 +107,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
                                           uint32_t limit = kWaitLimit) {
     for (uint32_t i = 0; i < limit; ++i) {
         if (mbar_try(bar, parity)) return true;
-        if (abort && (i & 255u) == 255u && *abort) return false;
+        if (abort && (i & 15u) == 15u && *abort) return false;
     }
     return false;
 }
