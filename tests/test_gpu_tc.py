@@ -84,6 +84,27 @@ def test_tc_several_rhs_blocks(nrhs):
     assert err.max() <= TOL, err
 
 
+@pytest.mark.parametrize("n", [1, 2, 7, 33, 500])
+def test_tc_tiny_plans_and_single_rhs(n):
+    """Few points: units with fewer source groups than G sets (padding entries), boxes of one point, and a
+    single right-hand side through the tensor-core path (RHS rows padded with zeros)."""
+    api = _api()
+    rng = np.random.default_rng(n)
+    pts = rng.random((n, 3)).astype(np.float32)
+    ng = 3
+    lo, h, k = (0.0, 0.0, 0.0), 1.0 / ng, 2 * np.pi * 1.5
+    plan = api.Plan(torch.from_numpy(pts).cuda(), lo, h, ng, k, max_nrhs=16)
+    for nrhs in (1, 16):
+        lam = W.strengths(n, nrhs, n + nrhs).reshape(n, nrhs)
+        out = plan.apply(torch.from_numpy(lam).cuda(), path="tc_bf16x3").cpu().numpy().reshape(n, nrhs)
+        assert plan.async_status() == 0
+        ref = oracle.p2p(pts, lam, lo, h, ng, k).reshape(n, nrhs)
+        if not np.linalg.norm(ref):
+            np.testing.assert_array_equal(out, 0)  # no pair with r > 0 (one point, or no neighbouring boxes)
+            continue
+        assert rel_l2(out, ref).max() <= TOL
+
+
 def test_tc_dense_boxes_and_adjoint():
     """Boxes with more than 64 targets take several target groups."""
     api = _api()
