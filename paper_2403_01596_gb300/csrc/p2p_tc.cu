@@ -498,7 +498,10 @@ __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
     volatile int* abort = sm.abort;
     const int t_off = slot_t_off(a.rb_count), b_off = slot_b_off(a.rb_count, a.tg);
     const int b_half = slot_b_half(a.tg), meta_off = slot_meta_off(a.rb_count, a.tg);
+    // this thread's task in the current unit: target t, sources h sp .. h sp + sp - 1 (set at the unit's first quad)
     float4 tx = make_float4(0.f, 0.f, 0.f, 0.f);
+    int T = 8, sp = 1, t = 0, h = 0;
+    bool act = false;
     Ring r{0, 0u};
     while (true) {
         const int idx = set * a.slots + r.slot;
@@ -509,18 +512,22 @@ __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
         }
         const int4 m = *reinterpret_cast<const int4*>(base + meta_off);
         if (m.y & kDone) break;
-        if (m.x >= 0) {
-            const int T = (m.z + 7) & ~7;
+        if (m.y & kFirst) {
+            T = (m.z + 7) & ~7;
             // sources per task: the smallest power of two with 16 T / SP <= 128 tasks
-            const int sp = T <= 8 ? 1 : (T <= 16 ? 2 : (T <= 32 ? 4 : 8));
-            const int tasks = kSrcGroup * T / sp;
-            const int t = i % T, h = i / T;
-            const float4* sx = reinterpret_cast<const float4*>(base + kImage * a.rb_count);
-            if (m.y & kFirst) {
+            sp = T <= 8 ? 1 : (T <= 16 ? 2 : (T <= 32 ? 4 : 8));
+            t = i % T;
+            h = i / T;
+            act = i < kSrcGroup * T / sp;
+            // the targets travel with the real stages of the first quad
+            if (m.x >= 0) {
                 const float4* st = reinterpret_cast<const float4*>(base + t_off);
                 tx = t < m.z ? st[t] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            if (i < tasks) {
+        }
+        if (m.x >= 0) {
+            const float4* sx = reinterpret_cast<const float4*>(base + kImage * a.rb_count);
+            if (act) {
                 unsigned char* b_hi = base + b_off;
                 unsigned char* b_lo = b_hi + b_half;
                 if (sp == 8) g_tile<KERN, 8>(sx, tx, t, h, T, b_hi, b_lo, a.k);
