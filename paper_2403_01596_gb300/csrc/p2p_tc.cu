@@ -25,13 +25,13 @@
 // Main kernel (k_p2p_tc): persistent, one CTA per SM, units (box, target group)
 // round robin over the CTAs in Morton order (neighbouring CTAs share records in
 // L2).  Warp roles:
-//   warp 0       producer: walks a unit's group list four entries at a time; lane s issues entry 4q + s
-//                into a slot of G set s (metadata, TMA bulk copy of the record, the unit's targets with
-//                the first quad)
-//   warps 1-16   four G sets of four warps: G tile in FP32, BF16 hi/lo split into the slot's B operand
-//   warps 17-20  one MMA issuer per set (one thread): once the set has written B, the three MMAs (per RHS
+//   warps 0-3    one producer per G set: walks a unit's group list four entries at a time and issues
+//                entry 4q + s into a slot of set s (metadata, TMA bulk copy of the record, the unit's
+//                targets with the first quad)
+//   warps 4-19   four G sets of four warps: G tile in FP32, BF16 hi/lo split into the slot's B operand
+//   warps 20-23  one MMA issuer per set (one thread): once the set has written B, the three MMAs (per RHS
 //                block) into the set's own accumulator, committed to the slot's release barrier
-//   warps 21-24  epilogue: sums the sets' accumulators (TMEM -> registers), combines Re/Im through
+//   warps 24-27  epilogue: sums the sets' accumulators (TMEM -> registers), combines Re/Im through
 //                shared memory and writes out[perm[t]]
 // Four independent issue chains (one per set) keep the tensor core fed with the
 // small (N = 2T) MMAs; two TMEM buffers alternate between a CTA's units so the
@@ -60,7 +60,7 @@ constexpr int kImage = 8192;           // hi + lo images of one 128 x 16 A opera
 constexpr int kLbo = 128, kSbo = 256;  // core-matrix strides (K direction, 8-row groups)
 constexpr int kSetCols = 256;          // TMEM columns of one unit buffer (an accumulator per G set)
 constexpr int kSets = 4;               // G sets of four warps; set s takes list entries s, s + kSets, ...
-constexpr int kGWarp0 = 1, kMmaWarp0 = kGWarp0 + 4 * kSets, kEpiWarp0 = kMmaWarp0 + kSets;
+constexpr int kGWarp0 = kSets, kMmaWarp0 = kGWarp0 + 4 * kSets, kEpiWarp0 = kMmaWarp0 + kSets;
 constexpr int kWarps = kEpiWarp0 + 4;
 constexpr int kThreads = kWarps * 32;
 // A waiting thread is suspended (up to kSuspendNs per poll) until the phase
@@ -391,12 +391,11 @@ struct Ring {
     }
 };
 
-// ---- producer (warp 0; lane s < kSets feeds set s) ----
+// ---- producer of set s (one warp; lane 0 issues) ----
 // A unit's group list is walked four entries (a quad) at a time, entry 4q + s going to set s.
-__device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, int lane) {
+__device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, int set, int lane) {
     volatile int* abort = sm.abort;
-    const bool active = lane < kSets;
-    const int set = active ? lane : 0;
+    const bool active = lane == 0;
     Ring r{0, 0u};
     const uint32_t rec = (uint32_t)record_bytes(a.rb_count);
     const int t_off = slot_t_off(a.rb_count), meta_off = slot_meta_off(a.rb_count, a.tg);
@@ -705,8 +704,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = *sm.tmem_slot;
     const int64_t units = (int64_t)a.nb * a.ngrp;
-    if (warp == 0) {
-        run_producer(a, sm, units, lane);
+    if (warp < kGWarp0) {
+        run_producer(a, sm, units, warp, lane);
     } else if (warp < kMmaWarp0) {
         const int gw = warp - kGWarp0;
         run_gset<KERN>(a, sm, gw >> 2, (gw & 3) * 32 + lane);
