@@ -437,10 +437,10 @@ def run_ours(args):
 
 
 # ------------------------------------------------------- extension workloads --
-# Non-default modes (python bench.py --workload multirhs|grad|batched): the
-# 64-RHS tensor-core comparison on the 2:1:1 ellipsoid, the differentiable
-# step on the sphere, and the batched uneven geometries.  Each prints one JSON
-# line of the same shape as the default occupancy sweep.
+# Non-default modes (python bench.py --workload cube|multirhs|grad|batched): the
+# dense cube, the 64-RHS tensor-core comparison on the 2:1:1 ellipsoid, the
+# differentiable step on the sphere, and the batched uneven geometries.  Each
+# prints one JSON line of the same shape as the default occupancy sweep.
 
 def _events_time(fn, steps, warmup, stream):
     import torch
@@ -642,6 +642,64 @@ def run_batched(args):
     return 0
 
 
+def run_cube(args):
+    """Dense uniform cube (32 768 points, 8^3 boxes, k = 8 pi), both source layouts: device-timed applies
+    (L2 flushed between them) and the full FP64 oracle on every target."""
+    import torch
+    from paper_2403_01596_gb300 import _capi as C, api, workloads as W
+    import oracle
+    torch.cuda.set_device(0)
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(0)
+    wl = W.cube_dense(int(32768 * args.scale), 0)
+    pts = torch.from_numpy(wl.points).cuda()
+    lam_np = W.strengths(wl.n, 1, wl.seed)
+    lam = torch.from_numpy(lam_np).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    oracle.build()
+    t = time.perf_counter()
+    ref = oracle.p2p(wl.points, lam_np, wl.lo, wl.h, wl.ng, wl.k)
+    cpu_s = time.perf_counter() - t
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = props.multi_processor_count * MUFU_LANES_PER_SM_CLK * f_max / MUFU_PER_PAIR["helmholtz"] / 1e9
+    res = {}
+    for layout in ("indexed", "redundant"):
+        plan = api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k, layout=layout)
+        out = torch.empty_like(lam)
+        P = plan.pair_count()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.ext_steps)]
+        for i in range(3 + args.ext_steps):
+            flush.zero_()
+            e = evs[i - 3] if i >= 3 else None
+            if e:
+                e[0].record(stream)
+            C.p2p_apply_stage(plan._plan, lam, 1, 1, C.P2P_PATH_FP32_SHARED, stream)
+            if e:
+                e[1].record(stream)
+            C.p2p_apply_staged(plan._plan, out, 1, 1, 0, C.P2P_PATH_FP32_SHARED, stream)
+            if e:
+                e[2].record(stream)
+        torch.cuda.synchronize()
+        apply_ms = statistics.median(e[0].elapsed_time(e[2]) for e in evs)
+        kern_ms = statistics.median(e[1].elapsed_time(e[2]) for e in evs)
+        err = float(np.linalg.norm(out.cpu().numpy() - ref) / np.linalg.norm(ref))
+        res[layout] = {"ms": apply_ms, "pair_kernel_ms": kern_ms, "gpair_s": P / apply_ms / 1e6,
+                       "pair_kernel_frac_of_mufu": P / kern_ms / 1e6 / peak, "rel_l2_vs_fp64": err}
+    line = {"metric": METRIC + " [dense cube]", "value": res["indexed"]["gpair_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.ext_steps, "warmup": 3, "ms_per_step": res["indexed"]["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "cube_uniform_8x8x8", "n_points": wl.n, "grid": wl.ng, "k": wl.k, "pairs": P,
+                       "l2": "flushed before every apply"},
+            "layouts": res,
+            "roofline": {"bound": "alu", "kernel": "k_pair", "achieved": P / res["indexed"]["pair_kernel_ms"] / 1e6,
+                         "peak": peak, "unit": "Gpair/s", "frac": res["indexed"]["pair_kernel_frac_of_mufu"]},
+            "cpu_baseline": {"value": P / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"full FP64 oracle on all {wl.n} targets ({P} pairs, {cpu_s:.1f} s)"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -654,7 +712,7 @@ def main():
     ap.add_argument("--target-group", type=int, default=0, help="targets per sweep (0: library default)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("sweep", "multirhs", "grad", "batched"), default="sweep",
+    ap.add_argument("--workload", choices=("sweep", "cube", "multirhs", "grad", "batched"), default="sweep",
                     help="sweep (default): the occupancy sweep; the others measure the extension paths")
     ap.add_argument("--scale", type=float, default=1.0, help="point-count scale of the extension workloads")
     ap.add_argument("--ext-steps", type=int, default=20)
@@ -665,6 +723,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "cube":
+        return run_cube(args)
     if args.workload == "multirhs":
         return run_multirhs(args)
     if args.workload == "grad":
