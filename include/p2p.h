@@ -83,10 +83,12 @@ typedef enum { P2P_LAYOUT_INDEXED = 0, P2P_LAYOUT_REDUNDANT = 1, P2P_LAYOUT_SYMM
 
 /* Evaluation path of p2p_apply_path (the plain p2p_apply picks P2P_PATH_AUTO). */
 typedef enum {
-    P2P_PATH_AUTO = 0,        /* FP32 shared-G for nrhs < 16, tensor-core path otherwise */
+    P2P_PATH_AUTO = 0,        /* FP32 shared-G for nrhs < 16, tensor-core path otherwise (when available) */
     P2P_PATH_FP32_PER_RHS = 1,/* FP32; G re-evaluated for every right-hand side */
-    P2P_PATH_FP32_SHARED = 2, /* FP32; each G evaluated once and applied to up to 8 RHS */
-    P2P_PATH_TC_BF16X3 = 3    /* G tile split into BF16 hi + lo, 3 tcgen05 MMAs, FP32 accumulate */
+    P2P_PATH_FP32_SHARED = 2, /* FP32; each G evaluated once and applied to up to 4 RHS at a time */
+    P2P_PATH_TC_BF16X3 = 3    /* G tile and strengths split into BF16 hi + lo, 3 tcgen05 MMAs per 16
+                                 sources, FP32 accumulation in tensor memory; plans with max_nrhs >= 16
+                                 on an sm_103 device, else P2P_ERR_UNSUPPORTED */
 } p2p_path;
 
 /* Launch tuning of a plan (the autotuner's knobs).  Zero fields take defaults. */
@@ -211,7 +213,10 @@ P2P_API p2p_status p2p_build_neighbors(const int64_t* box_keys, const int32_t* b
  *   nnz, sources                 from p2p_build_neighbors
  *   kernel, k                    Green's function and wavenumber (k finite; ignored for Laplace)
  *   layout                       source layout
- *   max_nrhs                     largest nrhs any apply on this plan will use, 1..256
+ *   max_nrhs                     largest nrhs any apply on this plan will use, 1..256; from 16 up
+ *                                the workspace also holds the tensor-core path's per-box group lists
+ *                                and its strength records, (n / 16 + num_boxes) x
+ *                                (ceil(max_nrhs / 64) x 8192 + 256) bytes
  *   tuning                 [host] NULL for defaults
  *   workspace              [dev] at least p2p_plan_workspace_size bytes, 256-byte aligned;
  *                                owned by the caller, must outlive the plan
@@ -267,10 +272,12 @@ P2P_API p2p_status p2p_apply_path(const p2p_plan* plan, const void* lambda, void
  * The two phases of p2p_apply_path, for callers that overlap or time them
  * separately.  p2p_apply_stage gathers lambda into the plan's staging buffer
  * in the order the chosen path reads it (box-sorted rows, or the per-box
- * packed rows of the redundant layout, Sec. 3.3); p2p_apply_staged then runs
- * the pair kernel on the staged strengths and writes out.  Both must be given
- * the same nrhs and path; no other call on the plan may come between them.
- * The arguments mean what they mean for p2p_apply_path.
+ * packed rows of the redundant layout, Sec. 3.3; for the tensor-core path, the
+ * BF16 hi/lo record of every 16-source group); p2p_apply_staged then runs the
+ * pair kernel (or the tensor-core kernel) on the staged strengths and writes
+ * out.  Both must be given the same nrhs and path; no other call on the plan
+ * may come between them.  The arguments mean what they mean for
+ * p2p_apply_path.
  */
 P2P_API p2p_status p2p_apply_stage(const p2p_plan* plan, const void* lambda, int32_t nrhs, int64_t ld, p2p_path path,
                                    p2p_stream_t stream);
