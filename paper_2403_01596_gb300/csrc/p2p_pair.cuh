@@ -266,6 +266,63 @@ __device__ __forceinline__ void pair_step(const float4* __restrict__ sx, const f
     }
 }
 
+// pair_step for an even number of targets per lane with the packed two-lane
+// FP32 instructions (add/mul/fma.f32x2): targets u and u + 1 share one register
+// pair in every operand, so coordinate differences, r^2, the phase, the
+// amplitude and the complex multiply-add issue once for two pairs; rsqrt and
+// sincos stay per pair.  Each packed operation rounds as its scalar
+// counterpart in pair_step, in the same order (the targets are kept negated so
+// that p - t is one add).
+template <int KERN, int R, int TT, bool MASK>
+__device__ __forceinline__ void pair_step_x2(const float4* __restrict__ sx, const float2* __restrict__ sl, int s,
+                                             const float2 (&nx)[TT / 2], const float2 (&ny)[TT / 2],
+                                             const float2 (&nz)[TT / 2], float2 (&ax)[TT / 2][R],
+                                             float2 (&ay)[TT / 2][R], float2 k2) {
+    const float4 p = sx[s];
+    const float2 px = make_float2(p.x, p.x), py = make_float2(p.y, p.y), pz = make_float2(p.z, p.z);
+    float2 lx[R], ly[R], nly[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float2 l = sl[s * R + r];
+        lx[r] = make_float2(l.x, l.x);
+        ly[r] = make_float2(l.y, l.y);
+        nly[r] = make_float2(-l.y, -l.y);
+    }
+#pragma unroll
+    for (int v = 0; v < TT / 2; ++v) {
+        const float2 dx = __fadd2_rn(px, nx[v]), dy = __fadd2_rn(py, ny[v]), dz = __fadd2_rn(pz, nz[v]);
+        float2 r2, inv;
+        if (MASK) {
+            r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            inv.x = r2.x > 0.f ? inv.x : 0.f;
+            inv.y = r2.y > 0.f ? inv.y : 0.f;
+        } else {
+            const float2 tiny = make_float2(1.17549435e-38f, 1.17549435e-38f);
+            r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, tiny)));
+            inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        }
+        if (KERN == P2P_HELMHOLTZ) {
+            const float2 ph = __fmul2_rn(k2, __fmul2_rn(r2, inv));
+            float2 sn, cs;
+            __sincosf(ph.x, &sn.x, &cs.x);
+            __sincosf(ph.y, &sn.y, &cs.y);
+            const float2 gr = __fmul2_rn(cs, inv), gi = __fmul2_rn(sn, inv);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ax[v][r] = __ffma2_rn(gr, lx[r], __ffma2_rn(gi, nly[r], ax[v][r]));
+                ay[v][r] = __ffma2_rn(gr, ly[r], __ffma2_rn(gi, lx[r], ay[v][r]));
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ax[v][r] = __ffma2_rn(inv, lx[r], ax[v][r]);
+                ay[v][r] = __ffma2_rn(inv, ly[r], ay[v][r]);
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int map_tt(int32_t m) { return m & 7; }
 __device__ __forceinline__ int map_g(int32_t m) { return (m >> 3) & 63; }
 __device__ __forceinline__ int map_q(int32_t m) { return (m >> 9) & 63; }
@@ -292,9 +349,33 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
     if (q < Q) {
         const float k = a.k;
         int s = q;
-        for (; s < m_end; s += Q) pair_step<KERN, R, TT, true>(sx, sl, s, tx, acc, k);  // own box: r = 0 possible
+        if constexpr (TT % 2 == 0) {
+            // targets in pairs for the packed two-lane instructions, accumulators (Re, Im) split by component
+            float2 nx[TT / 2], ny[TT / 2], nz[TT / 2], ax[TT / 2][R], ay[TT / 2][R];
+#pragma unroll
+            for (int v = 0; v < TT / 2; ++v) {
+                nx[v] = make_float2(-tx[2 * v].x, -tx[2 * v + 1].x);
+                ny[v] = make_float2(-tx[2 * v].y, -tx[2 * v + 1].y);
+                nz[v] = make_float2(-tx[2 * v].z, -tx[2 * v + 1].z);
+#pragma unroll
+                for (int r = 0; r < R; ++r) ax[v][r] = ay[v][r] = make_float2(0.f, 0.f);
+            }
+            const float2 k2 = make_float2(k, k);
+            for (; s < m_end; s += Q) pair_step_x2<KERN, R, TT, true>(sx, sl, s, nx, ny, nz, ax, ay, k2);
 #pragma unroll kPairUnroll
-        for (; s < ns; s += Q) pair_step<KERN, R, TT, false>(sx, sl, s, tx, acc, k);    // other boxes: r > 0
+            for (; s < ns; s += Q) pair_step_x2<KERN, R, TT, false>(sx, sl, s, nx, ny, nz, ax, ay, k2);
+#pragma unroll
+            for (int v = 0; v < TT / 2; ++v)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    acc[2 * v][r] = make_float2(ax[v][r].x, ay[v][r].x);
+                    acc[2 * v + 1][r] = make_float2(ax[v][r].y, ay[v][r].y);
+                }
+        } else {
+            for (; s < m_end; s += Q) pair_step<KERN, R, TT, true>(sx, sl, s, tx, acc, k);  // own box: r = 0 possible
+#pragma unroll kPairUnroll
+            for (; s < ns; s += Q) pair_step<KERN, R, TT, false>(sx, sl, s, tx, acc, k);    // other boxes: r > 0
+        }
     }
 #pragma unroll
     for (int u = 0; u < TT; ++u)
