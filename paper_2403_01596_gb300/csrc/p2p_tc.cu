@@ -467,25 +467,56 @@ __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, i
 }
 
 // ---- G sets (128 threads each); the set's first thread issues its MMAs ----
+// G tile part of one thread: target tx against sources h SP .. h SP + SP - 1.
+// For SP >= 2 the sources go in pairs through the packed two-lane FP32
+// instructions (each rounding as its scalar counterpart); rsqrt and sincos
+// stay per pair.  r = 0 and padding slots (w = 1) give 0.
 template <int KERN, int SP>
 __device__ __forceinline__ void g_tile(const float4* __restrict__ sx, float4 tx, int t, int h, int T,
                                        unsigned char* b_hi, unsigned char* b_lo, float k) {
     float re[SP], im[SP];
-#pragma unroll
-    for (int e = 0; e < SP; ++e) {
-        const float4 p = sx[h * SP + e];
+    if constexpr (SP == 1) {
+        const float4 p = sx[h];
         const float dx = p.x - tx.x, dy = p.y - tx.y, dz = p.z - tx.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float inv = rsqrtf(r2);
-        const bool ok = r2 > 0.f && p.w == 0.f;  // r = 0 skipped; padding slots give 0
+        const bool ok = r2 > 0.f && p.w == 0.f;
         if (KERN == P2P_LAPLACE) {
-            re[e] = ok ? inv : 0.f;
-            im[e] = 0.f;
+            re[0] = ok ? inv : 0.f;
+            im[0] = 0.f;
         } else {
             float sn, cs;
             __sincosf(k * (r2 * inv), &sn, &cs);
-            re[e] = ok ? cs * inv : 0.f;
-            im[e] = ok ? sn * inv : 0.f;
+            re[0] = ok ? cs * inv : 0.f;
+            im[0] = ok ? sn * inv : 0.f;
+        }
+    } else {
+        const float2 ntx = make_float2(-tx.x, -tx.x), nty = make_float2(-tx.y, -tx.y), ntz = make_float2(-tx.z, -tx.z);
+        const float2 k2 = make_float2(k, k);
+#pragma unroll
+        for (int e = 0; e < SP; e += 2) {
+            const float4 p0 = sx[h * SP + e], p1 = sx[h * SP + e + 1];
+            const float2 dx = __fadd2_rn(make_float2(p0.x, p1.x), ntx);
+            const float2 dy = __fadd2_rn(make_float2(p0.y, p1.y), nty);
+            const float2 dz = __fadd2_rn(make_float2(p0.z, p1.z), ntz);
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const bool ok0 = r2.x > 0.f && p0.w == 0.f, ok1 = r2.y > 0.f && p1.w == 0.f;
+            if (KERN == P2P_LAPLACE) {
+                re[e] = ok0 ? inv.x : 0.f;
+                re[e + 1] = ok1 ? inv.y : 0.f;
+                im[e] = im[e + 1] = 0.f;
+            } else {
+                const float2 ph = __fmul2_rn(k2, __fmul2_rn(r2, inv));
+                float2 sn, cs;
+                __sincosf(ph.x, &sn.x, &cs.x);
+                __sincosf(ph.y, &sn.y, &cs.y);
+                const float2 gr = __fmul2_rn(cs, inv), gi = __fmul2_rn(sn, inv);
+                re[e] = ok0 ? gr.x : 0.f;
+                re[e + 1] = ok1 ? gr.y : 0.f;
+                im[e] = ok0 ? gi.x : 0.f;
+                im[e + 1] = ok1 ? gi.y : 0.f;
+            }
         }
     }
     store_split<SP>(b_hi, b_lo, op_off(t, h * SP), re);
