@@ -45,6 +45,7 @@ OCCUPANCIES = (8, 16, 32, 64)
 MUFU_PER_PAIR = {"helmholtz": 3, "laplace": 1}  # rsqrt, sin, cos per Helmholtz pair
 MUFU_LANES_PER_SM_CLK = 16
 L2_FLUSH_BYTES = 256 << 20
+REFERENCE_BUDGET_S = 120.0  # oracle work of one --impl reference run (warm-up + timed steps)
 
 
 def _peaks() -> dict:
@@ -197,20 +198,27 @@ def run_reference(args):
     wls = sweep_workloads()
     structs = [_oracle_structure(wl) for wl in wls]
     lams = [W.strengths(wl.n, 1, wl.seed) for wl in wls]
-    per_density_s = 1.0
-    # size one step: ~per_density_s of oracle work per occupancy (t(m) = fixed + m * per_target)
-    samples = []
+    # size the samples so the whole run (warm-up + timed steps) takes about REFERENCE_BUDGET_S of oracle work;
+    # one oracle call costs t(m) = fixed + m * per_target for m sampled targets
+    steps_total = args.warmup + args.steps
+    step_budget = REFERENCE_BUDGET_S / max(steps_total, 1)
+    fixed, per_target = [], []
     for i, wl in enumerate(wls):
         t_small = _oracle_call_time(oracle, wl, lams[i], 256, 7)
         t_big = _oracle_call_time(oracle, wl, lams[i], 4096, 7)
-        per_target = max((t_big - t_small) / (4096 - 256), 1e-7)
-        fixed = max(t_small - 256 * per_target, 0.0)
-        samples.append(int(min(wl.n, max(256, (per_density_s - fixed) / per_target))))
+        per_target.append(max((t_big - t_small) / (4096 - 256), 1e-7))
+        fixed.append(max(t_small - 256 * per_target[-1], 0.0))
+    # every occupancy in every step while that fits the step's budget, else one occupancy per step in turn
+    rotate = step_budget < sum(fixed) + 4 * 256 * max(per_target)
+    share = step_budget if rotate else step_budget / len(wls)
+    samples = [int(min(wl.n, max(256, (share - fixed[i]) / per_target[i]))) for i, wl in enumerate(wls)]
     times, pairs = [], []
-    for step in range(args.warmup + args.steps):
+    for step in range(steps_total):
         t0 = time.perf_counter()
         p = 0
         for i, wl in enumerate(wls):
+            if rotate and i != step % len(wls):
+                continue
             targets = _sample_targets(wl.n, samples[i], 1000 + step)
             oracle.p2p_targets(wl.points, lams[i], targets, wl.lo, wl.h, wl.ng, wl.k)
             p += _sample_pairs(structs[i], wl.points, targets) if step >= args.warmup else 0
@@ -225,8 +233,10 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(args, "oracle"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"per step {samples} sampled targets (occupancy 8/16/32/64), FP64 single thread; "
-                                   "each call includes the oracle's own binning of all 2^20 points"},
+                         "sample": f"{samples} sampled targets at occupancy 8/16/32/64, "
+                                   + ("one occupancy per step in turn" if rotate else "all four per step")
+                                   + "; FP64 single thread; each call includes the oracle's own binning of all "
+                                     "2^20 points"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
