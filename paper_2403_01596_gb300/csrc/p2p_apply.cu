@@ -49,7 +49,72 @@ __device__ __forceinline__ void grad_targets(const PairArgs& a, const float4* __
         tgv[u] = ok ? a.gsrc[(int64_t)(tbase + t) * a.nrhs + rhs] : make_float2(0.f, 0.f);
         acc[u][0] = acc[u][1] = acc[u][2] = 0.f;
     }
-    if (q < Q) {
+    if (q < Q && TT % 2 == 0) {
+        // targets in pairs on the packed two-lane FP32 instructions (rsqrt, sincos per pair)
+        constexpr int V = TT / 2 > 0 ? TT / 2 : 1;
+        float2 px2[V], py2[V], pz2[V], lx2[V], ly2[V], gx2[V], gy2[V], ax[V], ay[V], az[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int u0 = 2 * v, u1 = (2 * v + 1) % TT;
+            px2[v] = make_float2(tx[u0].x, tx[u1].x);
+            py2[v] = make_float2(tx[u0].y, tx[u1].y);
+            pz2[v] = make_float2(tx[u0].z, tx[u1].z);
+            lx2[v] = make_float2(tl[u0].x, tl[u1].x);
+            ly2[v] = make_float2(tl[u0].y, tl[u1].y);
+            gx2[v] = make_float2(tgv[u0].x, tgv[u1].x);
+            gy2[v] = make_float2(tgv[u0].y, tgv[u1].y);
+            ax[v] = ay[v] = az[v] = make_float2(0.f, 0.f);
+        }
+        const float2 k2 = make_float2(a.k, a.k);
+        for (int s = q; s < ns; s += Q) {
+            const float4 p = sx[s];
+            const float4 lg = slg[s];  // (lambda_s.re, lambda_s.im, g_s.re, g_s.im)
+            const float2 npx = make_float2(-p.x, -p.x), npy = make_float2(-p.y, -p.y), npz = make_float2(-p.z, -p.z);
+            const float2 sl_x = make_float2(lg.x, lg.x), sl_y = make_float2(lg.y, lg.y);
+            const float2 sg_x = make_float2(lg.z, lg.z), sg_y = make_float2(lg.w, lg.w);
+            const float2 nsl_x = make_float2(-lg.x, -lg.x), nsg_y = make_float2(-lg.w, -lg.w);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float2 dx = __fadd2_rn(px2[v], npx), dy = __fadd2_rn(py2[v], npy), dz = __fadd2_rn(pz2[v], npz);
+                const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                inv.x = r2.x > 0.f ? inv.x : 0.f;
+                inv.y = r2.y > 0.f ? inv.y : 0.f;
+                const float2 inv2 = __fmul2_rn(inv, inv);
+                // C = conj(g_t) lambda_s + conj(g_s) lambda_t
+                const float2 cr = __ffma2_rn(gx2[v], sl_x, __ffma2_rn(gy2[v], sl_y,
+                                  __ffma2_rn(sg_x, lx2[v], __fmul2_rn(sg_y, ly2[v]))));
+                const float2 ci = __ffma2_rn(gx2[v], sl_y, __ffma2_rn(gy2[v], nsl_x,
+                                  __ffma2_rn(sg_x, ly2[v], __fmul2_rn(nsg_y, lx2[v]))));
+                float2 w;
+                if (KERN == P2P_HELMHOLTZ) {
+                    const float2 kr = __fmul2_rn(k2, __fmul2_rn(r2, inv));
+                    float2 sn, cs;
+                    __sincosf(kr.x, &sn.x, &cs.x);
+                    __sincosf(kr.y, &sn.y, &cs.y);
+                    const float2 ncs = make_float2(-cs.x, -cs.y), nsn = make_float2(-sn.x, -sn.y);
+                    const float2 dgr = __fmul2_rn(__ffma2_rn(nsn, kr, ncs), inv2);
+                    const float2 dgi = __fmul2_rn(__ffma2_rn(cs, kr, nsn), inv2);
+                    w = __ffma2_rn(dgr, cr, __fmul2_rn(make_float2(-dgi.x, -dgi.y), ci));
+                } else {
+                    w = __fmul2_rn(make_float2(-inv2.x, -inv2.y), cr);
+                }
+                w = __fmul2_rn(w, inv);
+                ax[v] = __ffma2_rn(w, dx, ax[v]);
+                ay[v] = __ffma2_rn(w, dy, ay[v]);
+                az[v] = __ffma2_rn(w, dz, az[v]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            acc[2 * v][0] = ax[v].x;
+            acc[2 * v][1] = ay[v].x;
+            acc[2 * v][2] = az[v].x;
+            acc[(2 * v + 1) % TT][0] = ax[v].y;
+            acc[(2 * v + 1) % TT][1] = ay[v].y;
+            acc[(2 * v + 1) % TT][2] = az[v].y;
+        }
+    } else if (q < Q) {
         const float k = a.k;
         for (int s = q; s < ns; s += Q) {
             const float4 p = sx[s];
