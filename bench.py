@@ -269,7 +269,7 @@ def _traffic_for(kernel_src_hash: str, layout: str):
 
 def _kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("p2p_apply.cu", "p2p_pair.cuh", "p2p_internal.cuh"):
+    for f in ("p2p_apply.cu", "p2p_pair.cuh", "p2p_internal.cuh", "p2p_plan.cu"):
         h.update(open(os.path.join(ROOT, "paper_2403_01596_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

@@ -93,7 +93,7 @@ typedef enum {
 
 /* Launch tuning of a plan (the autotuner's knobs).  Zero fields take defaults. */
 typedef struct {
-    int32_t chunk;         /* sources staged per work item, multiple of 32, 32..1024 (default 128) */
+    int32_t chunk;         /* sources staged per work item, multiple of 32, 32..1024 (default 192) */
     int32_t warps_per_cta; /* warps per thread block of the pair kernel, 1..16 (default 8) */
     int32_t target_group;  /* targets swept per pass, multiple of 32, 32..128 (default 32) */
     int32_t reserved;

@@ -20,11 +20,12 @@ import statistics
 import threading
 
 DEFAULT_CANDIDATES = (
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 32},
     {"chunk": 128, "warps_per_cta": 8, "target_group": 32},
-    {"chunk": 128, "warps_per_cta": 4, "target_group": 32},
-    {"chunk": 64, "warps_per_cta": 8, "target_group": 32},
+    {"chunk": 160, "warps_per_cta": 8, "target_group": 32},
     {"chunk": 256, "warps_per_cta": 4, "target_group": 32},
-    {"chunk": 128, "warps_per_cta": 8, "target_group": 64},
+    {"chunk": 128, "warps_per_cta": 4, "target_group": 32},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 64},
 )
 
 DEFAULT_LAYOUTS = ("indexed", "redundant", "symmetric")

@@ -412,7 +412,7 @@ bool tuning_valid(const p2p_tuning& t) {
 }
 
 p2p_tuning resolve_tuning(const p2p_tuning* t) {
-    p2p_tuning r{128, 8, 32, 0};
+    p2p_tuning r{192, 8, 32, 0};
     if (t) {
         if (t->chunk) r.chunk = t->chunk;
         if (t->warps_per_cta) r.warps_per_cta = t->warps_per_cta;
