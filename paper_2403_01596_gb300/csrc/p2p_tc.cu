@@ -25,14 +25,15 @@
 // Main kernel (k_p2p_tc): persistent, one CTA per SM, units (box, target group)
 // round robin over the CTAs in Morton order (neighbouring CTAs share records in
 // L2).  Warp roles:
-//   warps 0-3    one producer per G set: walks a unit's group list four entries at a time and issues
-//                entry 4q + s into a slot of set s (metadata, TMA bulk copy of the record, the unit's
-//                targets with the first quad)
+//   warps 0-3    one producer per G set: walks a unit's group list four entries (a quad) at a time and
+//                issues entry 4q + s into a slot of set s (metadata, TMA bulk copy of the record, the
+//                unit's targets with the first quad)
 //   warps 4-19   four G sets of four warps: G tile in FP32, BF16 hi/lo split into the slot's B operand
 //   warps 20-23  one MMA issuer per set (one thread): once the set has written B, the three MMAs (per RHS
 //                block) into the set's own accumulator, committed to the slot's release barrier
 //   warps 24-27  epilogue: sums the sets' accumulators (TMEM -> registers), combines Re/Im through
 //                shared memory and writes out[perm[t]]
+// (with P2P_TC_SETS = 2: two producers, two sets of eight warps, entries taken in pairs)
 // Four independent issue chains (one per set) keep the tensor core fed with the
 // small (N = 2T) MMAs; two TMEM buffers alternate between a CTA's units so the
 // epilogue of one unit overlaps the MMAs of the next.
@@ -59,8 +60,16 @@ constexpr int kSrcGroup = 16;          // sources per stage (MMA K)
 constexpr int kImage = 8192;           // hi + lo images of one 128 x 16 A operand
 constexpr int kLbo = 128, kSbo = 256;  // core-matrix strides (K direction, 8-row groups)
 constexpr int kSetCols = 256;          // TMEM columns of one unit buffer (an accumulator per G set)
-constexpr int kSets = 4;               // G sets of four warps; set s takes list entries s, s + kSets, ...
-constexpr int kGWarp0 = kSets, kMmaWarp0 = kGWarp0 + 4 * kSets, kEpiWarp0 = kMmaWarp0 + kSets;
+// G sets (independent producer -> G -> MMA chains; 2 or 4, the group lists are
+// padded to multiples of 4).  Four sets of four warps measured twice as fast as
+// two sets of eight (units of up to 64 targets, half the stages).
+#ifndef P2P_TC_SETS
+#define P2P_TC_SETS 4
+#endif
+constexpr int kSets = P2P_TC_SETS;     // G sets; set s takes list entries s, s + kSets, ... of a unit
+constexpr int kSetWarps = 16 / kSets;  // warps of one G set
+constexpr int kSetThreads = 32 * kSetWarps;
+constexpr int kGWarp0 = kSets, kMmaWarp0 = kGWarp0 + kSetWarps * kSets, kEpiWarp0 = kMmaWarp0 + kSets;
 constexpr int kWarps = kEpiWarp0 + 4;
 constexpr int kThreads = kWarps * 32;
 // A waiting thread is suspended (up to kSuspendNs per poll) until the phase
@@ -342,7 +351,7 @@ struct TcSmem {
     unsigned char* slots;  // kSets x slots
     float2* epi;
     uint64_t* full;        // [kSets * slots] TMA bytes + producer arrival
-    uint64_t* full_b;      // [kSets * slots] the G set's 128 threads (B operand written)
+    uint64_t* full_b;      // [kSets * slots] the G set's threads (B operand written)
     uint64_t* empty;       // [kSets * slots] MMA commit
     uint64_t* acc_full;    // [2] one commit per set after a unit's last quad
     uint64_t* acc_empty;   // [2] the epilogue's 128 threads
@@ -410,7 +419,7 @@ __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, i
         for (int w0 = 0; w0 < len && !failed; w0 += 32) {
             // 32 entries of the list (8 quads) in the warp's lanes
             const int gl = w0 + lane < len ? a.glist[off + w0 + lane] : -1;
-            const int nq = min(8, (len - w0) / kSets);
+            const int nq = min(32 / kSets, (len - w0) / kSets);
             for (int q = 0; q < nq; ++q) {
                 const int g = __shfl_sync(P2P_FULL_MASK, gl, q * kSets + set);
                 bool ok = true;
@@ -422,7 +431,7 @@ __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, i
                 }
                 if (active) {
                     unsigned char* base = slot_base(r.slot);
-                    const int qq = (w0 >> 2) + q;
+                    const int qq = w0 / kSets + q;
                     const bool first = qq == 0, last = w0 + (q + 1) * kSets == len;
                     *reinterpret_cast<int4*>(base + meta_off) =
                         make_int4(g, (first ? kFirst : 0) | (last ? kLast : 0), nt, 0);
@@ -544,8 +553,9 @@ __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
         if (m.y & kDone) break;
         if (m.y & kFirst) {
             T = (m.z + 7) & ~7;
-            // sources per task: the smallest power of two with 16 T / SP <= 128 tasks
-            sp = T <= 8 ? 1 : (T <= 16 ? 2 : (T <= 32 ? 4 : 8));
+            // sources per task: the smallest power of two with 16 T / SP <= kSetThreads tasks
+            sp = 1;
+            while (kSrcGroup * T > sp * kSetThreads) sp <<= 1;
             t = i % T;
             h = i / T;
             act = i < kSrcGroup * T / sp;
@@ -720,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ 
     if (tid == 32) {
         for (int i = 0; i < kSets * a.slots; ++i) {
             mbar_init(&sm.full[i], 1);
-            mbar_init(&sm.full_b[i], 128);
+            mbar_init(&sm.full_b[i], kSetThreads);
             mbar_init(&sm.empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -739,7 +749,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ 
         run_producer(a, sm, units, warp, lane);
     } else if (warp < kMmaWarp0) {
         const int gw = warp - kGWarp0;
-        run_gset<KERN>(a, sm, gw >> 2, (gw & 3) * 32 + lane);
+        run_gset<KERN>(a, sm, gw / kSetWarps, (gw % kSetWarps) * 32 + lane);
     } else if (warp < kEpiWarp0) {
         if (lane == 0) run_mma(a, sm, tmem, warp - kMmaWarp0);
     } else {
@@ -848,7 +858,7 @@ TcShape tc_shape(int32_t nrhs, int optin) {
     s.tg = (kSetCols / (2 * kSets * s.rb_count)) / 8 * 8;
     if (s.tg > 64) s.tg = 64;
     s.slot_bytes = slot_bytes_for(s.rb_count, s.tg);
-    s.slots = 4;
+    s.slots = 8;
     while (s.slots > 1 && tc_smem_bytes(s.slots, s.slot_bytes) > optin) --s.slots;
     s.smem = tc_smem_bytes(s.slots, s.slot_bytes);
     // more than half an SM's shared memory keeps one CTA (and one 512-column TMEM allocation) per SM
