@@ -149,6 +149,104 @@ def _oracle_call_time(oracle, wl, lam, m, seed):
     return time.perf_counter() - t
 
 
+def _oracle_worker(occupancies, jobs, done, barrier):
+    """One host core of the all-cores oracle timing: rebuilds the seeded sweep workloads itself (no point data
+    crosses a pipe), then per request runs the unchanged oracle on its share of the sampled targets, started
+    together with the other workers by a barrier."""
+    import oracle
+    from paper_2403_01596_gb300 import workloads as W
+    oracle.build()
+    wls = [W.sphere_density(d) for d in occupancies]
+    lams = [W.strengths(wl.n, 1, wl.seed) for wl in wls]
+    oracle.p2p_targets(wls[0].points, lams[0], np.arange(4), wls[0].lo, wls[0].h, wls[0].ng, wls[0].k)
+    done.put("ready")
+    while True:
+        job = jobs.get()
+        if job is None:
+            return
+        i, targets = job
+        barrier.wait(timeout=900)
+        wl = wls[i]
+        oracle.p2p_targets(wl.points, lams[i], targets, wl.lo, wl.h, wl.ng, wl.k)
+        done.put(len(targets))
+
+
+class OraclePool:
+    """The FP64 oracle, as it stands (single-threaded C), run as one spawned process per host core on disjoint
+    target shares of the occupancy sweep; run() returns the wall time from the common start to the last finish."""
+
+    def __init__(self, workers: int | None = None):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")  # the parent may hold a CUDA context: no fork
+        self.workers = max(1, workers or os.cpu_count() or 1)
+        self.done = ctx.Queue()
+        self.barrier = ctx.Barrier(self.workers + 1)
+        self.jobs = [ctx.Queue() for _ in range(self.workers)]
+        self.procs = [ctx.Process(target=_oracle_worker, args=(OCCUPANCIES, q, self.done, self.barrier),
+                                  daemon=True) for q in self.jobs]
+        for pr in self.procs:
+            pr.start()
+        self._collect()
+
+    def _collect(self):
+        """One message from every worker; raises as soon as a worker has died."""
+        import queue
+        got = 0
+        while got < self.workers:
+            try:
+                self.done.get(timeout=1.0)
+                got += 1
+            except queue.Empty:
+                dead = [pr.exitcode for pr in self.procs if not pr.is_alive()]
+                if dead:
+                    self.close()
+                    raise RuntimeError(f"oracle worker exited with {dead[0]}")
+
+    def run(self, i: int, targets) -> float:
+        for q, share in zip(self.jobs, np.array_split(np.asarray(targets), self.workers)):
+            q.put((i, share))
+        self.barrier.wait(timeout=900)
+        t = time.perf_counter()
+        self._collect()
+        return time.perf_counter() - t
+
+    def close(self):
+        for q in self.jobs:
+            q.put(None)
+        for pr in self.procs:
+            pr.join(timeout=60)
+            if pr.is_alive():
+                pr.terminate()
+
+
+def _sample_pairs_fast(struct_host, points, targets) -> int:
+    """_sample_pairs without the per-target loop when the point set has no repeated coordinates (every target's
+    only r = 0 pair is with itself)."""
+    box_ptr, nbr_ptr, nbr_idx, point_box, perm = struct_host
+    if np.unique(points, axis=0).shape[0] != points.shape[0]:
+        return _sample_pairs(struct_host, points, targets)
+    sizes = np.diff(box_ptr).astype(np.int64)
+    per_box = np.add.reduceat(sizes[nbr_idx], nbr_ptr[:-1]) if len(nbr_idx) else np.zeros(len(sizes), np.int64)
+    return int((per_box[point_box[targets]] - 1).sum())
+
+
+def cpu_oracle_all_cores(wls, structs, calib, seconds_per_density: float, seed: int):
+    """The oracle on every host core (OraclePool), each core given about seconds_per_density of work per
+    occupancy (calib = the single-thread (fixed, per-target) cost of one oracle call)."""
+    pool = OraclePool()
+    try:
+        pairs, seconds = 0, 0.0
+        for i, (wl, st) in enumerate(zip(wls, structs)):
+            fixed, per_target = calib[i]
+            m = int(min(wl.n // pool.workers, max(512, (seconds_per_density - fixed) / per_target)))
+            targets = _sample_targets(wl.n, m * pool.workers, seed + 7 + i)
+            seconds += pool.run(i, targets)
+            pairs += _sample_pairs_fast(st, wl.points, targets)
+    finally:
+        pool.close()
+    return {"pairs": pairs, "seconds": seconds, "workers": pool.workers}
+
+
 def cpu_oracle_sample(wls, structs, seconds_per_density: float, seed: int):
     """Times the FP64 oracle (as it stands, single thread) on sampled targets."""
     import oracle
@@ -168,7 +266,7 @@ def cpu_oracle_sample(wls, structs, seconds_per_density: float, seed: int):
         dt = time.perf_counter() - t
         pairs = _sample_pairs(st, wl.points, targets)
         res.append({"occupancy": wl.meta["target_occupancy"], "targets": targets, "ref": ref, "seconds": dt,
-                    "pairs": pairs})
+                    "pairs": pairs, "calib": (fixed, per_target)})
     return res
 
 
@@ -211,32 +309,38 @@ def run_reference(args):
     # every occupancy in every step while that fits the step's budget, else one occupancy per step in turn
     rotate = step_budget < sum(fixed) + 4 * 256 * max(per_target)
     share = step_budget if rotate else step_budget / len(wls)
-    samples = [int(min(wl.n, max(256, (share - fixed[i]) / per_target[i]))) for i, wl in enumerate(wls)]
+    # every host core runs the oracle on its own share of each step's targets (OraclePool), each core about the
+    # single-thread budget's worth
+    pool = OraclePool()
+    workers = pool.workers
+    samples = [int(min(wl.n // workers, max(256, (share - fixed[i]) / per_target[i]))) * workers
+               for i, wl in enumerate(wls)]
     times, pairs = [], []
-    for step in range(steps_total):
-        t0 = time.perf_counter()
-        p = 0
-        for i, wl in enumerate(wls):
-            if rotate and i != step % len(wls):
-                continue
-            targets = _sample_targets(wl.n, samples[i], 1000 + step)
-            oracle.p2p_targets(wl.points, lams[i], targets, wl.lo, wl.h, wl.ng, wl.k)
-            p += _sample_pairs(structs[i], wl.points, targets) if step >= args.warmup else 0
-        dt = time.perf_counter() - t0
-        if step >= args.warmup:
-            times.append(dt)
-            pairs.append(p)
+    try:
+        for step in range(steps_total):
+            dt, p = 0.0, 0
+            for i, wl in enumerate(wls):
+                if rotate and i != step % len(wls):
+                    continue
+                targets = _sample_targets(wl.n, samples[i], 1000 + step)
+                dt += pool.run(i, targets)
+                p += _sample_pairs_fast(structs[i], wl.points, targets) if step >= args.warmup else 0
+            if step >= args.warmup:
+                times.append(dt)
+                pairs.append(p)
+    finally:
+        pool.close()
     value = sum(pairs) / sum(times) / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(args, "oracle"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                          "sample": f"{samples} sampled targets at occupancy 8/16/32/64, "
                                    + ("one occupancy per step in turn" if rotate else "all four per step")
-                                   + "; FP64 single thread; each call includes the oracle's own binning of all "
-                                     "2^20 points"},
+                                   + f"; FP64 oracle as one process per core ({workers}) on disjoint shares, wall "
+                                     "time; each call includes the oracle's own binning of all 2^20 points"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -417,10 +521,17 @@ def run_ours(args):
         res = cpu_oracle_sample(wls, structs, args.cpu_seconds / len(wls), 17)
         cpu_pairs = sum(r["pairs"] for r in res)
         cpu_s = sum(r["seconds"] for r in res)
-        cpu = {"value": cpu_pairs / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "FP64 oracle on " + ", ".join(f"{len(r['targets'])} targets at occupancy {r['occupancy']}"
-                                                       for r in res) + f" ({cpu_pairs} pairs, {cpu_s:.1f} s; each call "
-                                                                       "includes the oracle's own binning of all 2^20 points)"}
+        single = cpu_pairs / cpu_s / 1e9
+        allc = cpu_oracle_all_cores(wls, structs, [r["calib"] for r in res], args.cpu_seconds / len(wls), 17)
+        cpu = {"value": allc["pairs"] / allc["seconds"] / 1e9, "unit": UNIT, "cores": allc["workers"],
+               "kind": "oracle",
+               "sample": f"FP64 oracle as one process per core ({allc['workers']}) on disjoint sampled targets, "
+                         f"{allc['pairs']} pairs in {allc['seconds']:.1f} s wall; each call includes the oracle's own "
+                         "binning of all 2^20 points",
+               "single_thread": {"value": single, "cores": 1,
+                                 "sample": "FP64 oracle on " + ", ".join(
+                                     f"{len(r['targets'])} targets at occupancy {r['occupancy']}" for r in res)
+                                           + f" ({cpu_pairs} pairs, {cpu_s:.1f} s)"}}
         errs = []
         for r, out in zip(res, outs):
             got = out.cpu().numpy()[r["targets"]]
