@@ -338,6 +338,42 @@ P2P_API p2p_status p2p_batch_info(const p2p_batch* batch, int64_t* work_items, i
                                   int32_t* warps_per_cta);
 P2P_API p2p_status p2p_batch_destroy(p2p_batch* batch);
 
+/* ------------------------------------------------- host-buffer apply --- */
+/*
+ * out_g = A_g lambda_g for a sequence of plans g = 0 .. count-1 whose strengths
+ * and results live in host memory.  Each plan's strengths are copied into one of
+ * two device staging slots, gathered and applied (as p2p_apply, path AUTO), and
+ * the results copied back; the copies run on the pipe's own copy stream, so the
+ * upload of plan g+1 and the download of plan g-1 overlap the kernels of plan g.
+ *
+ *   max_n            largest plan size (points) the pipe will carry, >= 1
+ *   nrhs             right-hand sides per point, 1 .. 256
+ *   workspace  [dev] at least p2p_host_pipe_workspace_size bytes, 256-byte aligned
+ *                    (two strength slots and two result slots of max_n x nrhs
+ *                    complex64)
+ *   lambdas    [host] count host pointers; lambdas[g] is plan g's n_g x nrhs
+ *                    complex64 strengths, contiguous (ld = nrhs)
+ *   outs       [host] count host pointers, same shape; fully overwritten
+ *   count            1 .. 64; every plan has n_g <= max_n and max_nrhs >= nrhs
+ *
+ * Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister); pageable
+ * memory gives the same results without the overlap.  p2p_apply_host enqueues
+ * everything and returns; the outs are complete once `stream` reaches the end of
+ * the call (the caller's stream waits for the last download), so synchronising
+ * `stream`, or an event recorded on it after the call, covers them.  Calls on one
+ * pipe must be issued on one stream; the plans must not be applied concurrently
+ * elsewhere meanwhile (they share their staging buffers).  p2p_host_pipe_create
+ * creates the copy stream and events (host-side objects released by
+ * p2p_host_pipe_destroy, which synchronises the copy stream first).
+ */
+typedef struct p2p_host_pipe p2p_host_pipe;
+P2P_API p2p_status p2p_host_pipe_workspace_size(int64_t max_n, int32_t nrhs, size_t* bytes);
+P2P_API p2p_status p2p_host_pipe_create(p2p_host_pipe** pipe, int64_t max_n, int32_t nrhs, void* workspace,
+                                        size_t workspace_bytes);
+P2P_API p2p_status p2p_apply_host(p2p_host_pipe* pipe, const p2p_plan* const* plans, int32_t count,
+                                  const void* const* lambdas, void* const* outs, p2p_stream_t stream);
+P2P_API p2p_status p2p_host_pipe_destroy(p2p_host_pipe* pipe);
+
 /*
  * Self-check of the tensor-core operand path (not part of the operator): one
  * thread block computes D = A . B^T through the same BF16 hi/lo split, shared-

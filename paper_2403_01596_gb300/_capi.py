@@ -99,6 +99,10 @@ def load(build_if_missing: bool = True):
             "p2p_batch_graph_launch": ([P, P], ctypes.c_int),
             "p2p_batch_info": ([P, PI64, PI32, PI32], ctypes.c_int),
             "p2p_batch_destroy": ([P], ctypes.c_int),
+            "p2p_host_pipe_workspace_size": ([i64, i32, PSZ], ctypes.c_int),
+            "p2p_host_pipe_create": ([ctypes.POINTER(P), i64, i32, P, sz], ctypes.c_int),
+            "p2p_apply_host": ([P, P, i32, P, P, P], ctypes.c_int),
+            "p2p_host_pipe_destroy": ([P], ctypes.c_int),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -302,3 +306,26 @@ def p2p_batch_destroy(batch):
 
 def p2p_diag_wait_timeout(status, limit, stream=None):
     check(load().p2p_diag_wait_timeout(_ptr(status), int(limit), _stream(stream)), "p2p_diag_wait_timeout")
+
+
+def p2p_host_pipe_workspace_size(max_n, nrhs) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().p2p_host_pipe_workspace_size(int(max_n), int(nrhs), ctypes.byref(out)), "p2p_host_pipe_workspace_size")
+    return out.value
+
+
+def p2p_host_pipe_create(max_n, nrhs, workspace):
+    pipe = ctypes.c_void_p(0)
+    check(load().p2p_host_pipe_create(ctypes.byref(pipe), int(max_n), int(nrhs), _ptr(workspace), workspace.numel()),
+          "p2p_host_pipe_create")
+    return pipe
+
+
+def p2p_apply_host(pipe, plans, lams_host, outs_host, stream=None):
+    check(load().p2p_apply_host(pipe, _ptr_array(plans), len(plans), _ptr_array(lams_host), _ptr_array(outs_host),
+                                _stream(stream)), "p2p_apply_host")
+
+
+def p2p_host_pipe_destroy(pipe):
+    if pipe:
+        load().p2p_host_pipe_destroy(pipe)

@@ -203,6 +203,49 @@ class Batch:
             pass
 
 
+class HostPipe:
+    """Applies a sequence of plans to strengths held in (page-locked) host memory and writes the results back
+    to host memory; uploads and downloads of neighbouring plans overlap each plan's kernels."""
+
+    def __init__(self, max_n: int, nrhs: int = 1, device=None):
+        self.max_n = int(max_n)
+        self.nrhs = int(nrhs)
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.workspace = _bytes(C.p2p_host_pipe_workspace_size(self.max_n, self.nrhs), dev)
+        self._p = C.p2p_host_pipe_create(self.max_n, self.nrhs, self.workspace)
+
+    def apply(self, plans, lams_host, outs_host=None):
+        """lams_host[g]: plan g's (n_g,) or (n_g, nrhs) complex64 CPU tensor; returns the CPU results, complete
+        once the current stream has reached this call's end."""
+        if len(lams_host) != len(plans):
+            raise ValueError("one strength tensor per plan is required")
+        lam2 = []
+        for p, l in zip(plans, lams_host):
+            if l.device.type != "cpu" or l.dtype != torch.complex64 or not l.is_contiguous():
+                raise ValueError("host strengths must be contiguous complex64 CPU tensors")
+            if l.numel() != p.n * self.nrhs:
+                raise ValueError(f"expected {p.n} x {self.nrhs} strengths")
+            lam2.append(l)
+        if outs_host is None:
+            outs_host = [torch.empty_like(l, pin_memory=True) for l in lam2]
+        for o, l in zip(outs_host, lam2):
+            if o.device.type != "cpu" or o.dtype != torch.complex64 or not o.is_contiguous() or o.numel() != l.numel():
+                raise ValueError("host results must be contiguous complex64 CPU tensors shaped like the strengths")
+        C.p2p_apply_host(self._p, [p._plan for p in plans], lam2, outs_host, _stream())
+        return outs_host
+
+    def close(self):
+        if getattr(self, "_p", None):
+            C.p2p_host_pipe_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def choose_grid_ct(points: torch.Tensor, lo, extent: float, ct: int, ng_start: int = 1,
                    ng_max: int = 1 << 21) -> BoxStructure:
     """Leaf grid by clustering threshold (Sec. 3.1): raise the tree level, doubling

@@ -85,3 +85,19 @@ def test_invalid_arguments_rejected_on_host(lib):
     plan = ctypes.c_void_p(0)
     assert lib.p2p_plan_create(ctypes.byref(plan), None, 10, None, None, 0, None, None, 0, 0, 0, 1.0, 0, 1, None,
                                None, 0, None) == 1
+
+
+def test_host_pipe_arguments_rejected_on_host(lib):
+    out = ctypes.c_size_t(0)
+    assert lib.p2p_host_pipe_workspace_size(0, 1, ctypes.byref(out)) == 1           # no points
+    assert lib.p2p_host_pipe_workspace_size(100, 0, ctypes.byref(out)) == 1         # nrhs 0
+    assert lib.p2p_host_pipe_workspace_size(100, 257, ctypes.byref(out)) == 1       # nrhs too big
+    assert lib.p2p_host_pipe_workspace_size(1000, 4, ctypes.byref(out)) == 0
+    assert out.value >= 4 * 1000 * 4 * 8                                             # 2 strength + 2 result slots
+    pipe = ctypes.c_void_p(0)
+    assert lib.p2p_host_pipe_create(ctypes.byref(pipe), 1000, 4, None, out.value) == 1          # no workspace
+    assert lib.p2p_host_pipe_create(ctypes.byref(pipe), 1000, 4, ctypes.c_void_p(256), 16) == 2  # too small
+    assert lib.p2p_host_pipe_create(ctypes.byref(pipe), 1000, 4, ctypes.c_void_p(8), out.value) == 1  # unaligned
+    assert not pipe.value
+    assert lib.p2p_apply_host(None, None, 1, None, None, None) == 1
+    assert lib.p2p_host_pipe_destroy(None) == 0
