@@ -336,6 +336,8 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
     const int G = map_g(map), Q = map_q(map);
     const int q = map_div(map, lane);
     const int g = lane - q * G;
+    // output row of the lane's first target, loaded now so the sweep hides its latency
+    const int32_t perm0 = lane < nt ? a.perm[tbase + lane] : 0;
     float4 tx[TT];
     float2 acc[TT][R];
 #pragma unroll
@@ -397,7 +399,7 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
                 v[r].y += w.y;
             }
         }
-        const int64_t row = (int64_t)a.perm[tbase + t] * a.ld + rb;
+        const int64_t row = (int64_t)(t == lane ? perm0 : a.perm[tbase + t]) * a.ld + rb;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (rb + r < a.nrhs) {
