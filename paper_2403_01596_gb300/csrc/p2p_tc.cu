@@ -556,9 +556,12 @@ __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
             // sources per task: the smallest power of two with 16 T / SP <= kSetThreads tasks
             sp = 1;
             while (kSrcGroup * T > sp * kSetThreads) sp <<= 1;
-            t = i % T;
-            h = i / T;
-            act = i < kSrcGroup * T / sp;
+            // eight consecutive threads take eight consecutive targets (rows of one 8-row core matrix) and the
+            // next bits the source slices, so a warp's B stores fill whole core matrices (no bank conflicts)
+            const int rest = i >> 3, H = kSrcGroup / sp;
+            h = rest % H;
+            t = (rest / H) * 8 + (i & 7);
+            act = t < T;
             // the targets travel with the real stages of the first quad
             if (m.x >= 0) {
                 const float4* st = reinterpret_cast<const float4*>(base + t_off);
