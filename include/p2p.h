@@ -388,6 +388,11 @@ P2P_API p2p_status p2p_host_pipe_destroy(p2p_host_pipe* pipe);
  */
 P2P_API p2p_status p2p_diag_tc_gemm(const float* A, const float* B, float* D, int32_t K, int32_t n,
                                     unsigned int* status, p2p_stream_t stream);
+/* The same product with A's hi and lo slices written to tensor memory (row m in
+ * lane m, K elements packed two per 32-bit column) and read from there by the
+ * MMAs, the operand path of the multi-RHS kernel's strengths.  Same arguments. */
+P2P_API p2p_status p2p_diag_tc_gemm_tmem_a(const float* A, const float* B, float* D, int32_t K, int32_t n,
+                                           unsigned int* status, p2p_stream_t stream);
 
 /*
  * Self-check of the bounded waits (not part of the operator): one warp waits

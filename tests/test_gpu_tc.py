@@ -29,8 +29,9 @@ def rel_l2(x, ref):
     return np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0)
 
 
+@pytest.mark.parametrize("a_in_tmem", [False, True])
 @pytest.mark.parametrize("n,K", [(16, 64), (64, 128), (256, 192), (48, 320)])
-def test_tc_operand_layout(n, K):
+def test_tc_operand_layout(n, K, a_in_tmem):
     _api()
     from paper_2403_01596_gb300 import _capi as C
     g = torch.Generator().manual_seed(n + K)
@@ -38,7 +39,7 @@ def test_tc_operand_layout(n, K):
     B = torch.randn(n, K, generator=g, dtype=torch.float32)
     D = torch.empty(128, n, dtype=torch.float32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    C.p2p_diag_tc_gemm(A.cuda(), B.cuda(), D, status)
+    C.p2p_diag_tc_gemm(A.cuda(), B.cuda(), D, status, a_in_tmem=a_in_tmem)
     torch.cuda.synchronize()
     assert int(status.item()) == 0
     ref = (A.double() @ B.double().T).numpy()
@@ -137,3 +138,18 @@ def test_tc_matches_fp32_paths_and_auto_dispatch():
     targets = np.random.default_rng(0).choice(wl.n, 500, replace=False)
     ref = oracle.p2p_targets(wl.points, lam.cpu().numpy(), targets, wl.lo, wl.h, wl.ng, wl.k)
     assert rel_l2(tc[targets], ref).max() <= TOL
+
+
+def test_tc_full_size_ellipsoid_sampled():
+    """The 64-RHS workload at full size (2^21 points on the 2:1:1 ellipsoid, 188^3 grid), in the launch
+    configuration the benchmark times: sampled targets against the oracle, every RHS."""
+    api = _api()
+    wl = W.ellipsoid_multirhs()
+    nrhs = 64
+    lam = W.strengths(wl.n, nrhs, 2).reshape(wl.n, nrhs)
+    plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, wl.k, max_nrhs=nrhs)
+    out = plan.apply(torch.from_numpy(lam).cuda(), path="tc_bf16x3").cpu().numpy()
+    assert plan.async_status() == 0
+    targets = np.random.default_rng(21).choice(wl.n, 400, replace=False)
+    ref = oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, wl.k)
+    assert rel_l2(out[targets], ref).max() <= TOL
