@@ -1,10 +1,11 @@
 // tcgen05.mma throughput microbenchmark (kind::f16, BF16 operands, FP32 accumulation, M = 128, K = 16).
 //
 // One block per SM; `issuers` threads (lane 0 of warps 0 .. issuers-1) each issue `iters` MMAs of width N back
-// to back into their own TMEM columns, with both operands in shared memory (zero-filled, the canonical K-major
-// layout without swizzle that the multi-RHS kernel uses: 8-row x 16-byte core matrices, LBO 128 B, SBO 256 B),
-// then commit to an mbarrier and wait for it (bounded). clock64 around the issue loop and the wait gives cycles
-// per MMA per issuer for block 0. Operand bytes per MMA are 4 KB (A) + N x 32 B (B).
+// to back into their own TMEM columns, then commit to an mbarrier and wait for it (bounded). B is in shared
+// memory (zero-filled, the canonical K-major layout without swizzle that the multi-RHS kernel uses: 8-row x
+// 16-byte core matrices, LBO 128 B, SBO 256 B); A is in shared memory the same way, or (second half of the
+// run) in tensor memory. clock64 around the issue loop and the wait gives cycles per MMA per issuer for block 0.
+// Operand bytes read from shared memory per MMA: 4 KB (A, when there) + N x 32 B (B).
 #include <cstdio>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -20,6 +21,10 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                  ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
 }
+__device__ __forceinline__ void mma_at(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+                 ::"r"(d), "r"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (uint32_t i = 0; i < (1u << 22); ++i) {
         uint32_t done;
@@ -30,9 +35,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-__global__ void __launch_bounds__(128, 1) k_bench(int n, int iters, int issuers, long long* out, unsigned* status) {
+__global__ void __launch_bounds__(128, 1) k_bench(int n, int iters, int issuers, int a_tmem, long long* out, unsigned* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    // A: 128 x 16 bf16 = 4 KB; B: up to 256 x 16 bf16 = 8 KB
+    // A: 128 x 16 bf16 = 4 KB; B: 256 x 16 bf16 = 8 KB (max N)
     unsigned char* A = smem;
     unsigned char* Bm = smem + 4096;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 4096 + 8192);
@@ -55,9 +60,14 @@ __global__ void __launch_bounds__(128, 1) k_bench(int n, int iters, int issuers,
     if ((tid & 31) == 0 && warp < issuers) {
         const uint64_t da = smem_desc(smem_u32(A)), db = smem_desc(smem_u32(Bm));
         const uint32_t id = idesc(n);
-        const uint32_t d = tmem + (uint32_t)(warp * (512 / issuers));  // disjoint columns per issuer (n <= 512 / issuers)
+        const uint32_t d = tmem + (uint32_t)(warp * ((a_tmem ? 256 : 512) / issuers));  // disjoint columns per issuer
+        const uint32_t at = tmem + 256u + (uint32_t)(warp * 16);                       // A operand columns (TMEM mode)
         long long t0 = clock64();
-        for (int i = 0; i < iters; ++i) mma(d, da, db, id, i > 0 ? 1u : 0u);
+        if (a_tmem) {
+            for (int i = 0; i < iters; ++i) mma_at(d, at, db, id, i > 0 ? 1u : 0u);
+        } else {
+            for (int i = 0; i < iters; ++i) mma(d, da, db, id, i > 0 ? 1u : 0u);
+        }
         long long t1 = clock64();
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&bar[warp])) : "memory");
         bool ok = mbar_wait(&bar[warp], 0);
@@ -86,21 +96,21 @@ int main() {
     int sms = 0; cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     const int iters = 256;
     int ns[] = {32, 64, 128, 256};
+    for (int a_tmem : {0, 1})
     for (int issuers : {1, 2, 4}) {
         for (int n : ns) {
-            if (issuers > 1 && n > 512 / (issuers) ) continue;
-            if (issuers == 4 && n > 128) continue;
-            if (issuers == 2 && n > 256) continue;
+            const int cols = a_tmem ? 256 : 512;
+            if (n > cols / issuers) continue;
             for (int rep = 0; rep < 2; ++rep) {
                 cudaMemset(out, 0, 64 * sizeof(long long));
-                k_bench<<<sms, 128, smem>>>(n, iters, issuers, out, status);
+                k_bench<<<sms, 128, smem>>>(n, iters, issuers, a_tmem, out, status);
                 cudaError_t e = cudaDeviceSynchronize();
                 if (e != cudaSuccess) { printf("error %s\n", cudaGetErrorString(e)); return 1; }
                 long long h[8]; unsigned st;
                 cudaMemcpy(h, out, sizeof(h), cudaMemcpyDeviceToHost);
                 cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost);
                 if (rep == 1) {
-                    printf("issuers %d N %3d: per-MMA issue", issuers, n);
+                    printf("A in %s issuers %d N %3d: per-MMA issue", a_tmem ? "TMEM" : "smem", issuers, n);
                     for (int w = 0; w < issuers; ++w) printf(" %.1f", (double)h[2 * w] / iters);
                     printf(" | issue+complete per MMA");
                     for (int w = 0; w < issuers; ++w) printf(" %.1f", (double)h[2 * w + 1] / iters);
