@@ -351,7 +351,8 @@ def _config(args, layout):
     return {"workload": "sphere_occupancy_sweep", "n_points": 1 << 20, "occupancies": list(OCCUPANCIES),
             "grids": [180, 124, 86, 61], "kernel": "helmholtz", "k": "2*pi/(4h)", "nrhs": 1, "layout": layout,
             "tuning": {"chunk": getattr(args, "chunk", 0), "warps_per_cta": getattr(args, "warps", 0),
-                       "target_group": getattr(args, "target_group", 0)},
+                       "target_group": getattr(args, "target_group", 0),
+                       "note": "0 = chosen by each plan; the launch tuning used is in roofline.per_occupancy"},
             "l2": "flushed between timed steps (256 MiB write, outside the timed events)"}
 
 
@@ -504,7 +505,8 @@ def run_ours(args):
         detail.append({"occupancy": wl.meta["target_occupancy"], "layout": layouts[i], "boxes": plans[i].num_boxes,
                        "pairs": pairs[i], "pair_kernel_ms": pm, "stage_ms": sm,
                        "gpair_s": pairs[i] / (pm + sm) / 1e6, "pair_kernel_frac_of_mufu": pairs[i] / pm / 1e6 / peak_pairs,
-                       "plan_s": t_plan[i], "work_items": plans[i].info["work_items"]})
+                       "plan_s": t_plan[i], "work_items": plans[i].info["work_items"],
+                       "tuning": plans[i].info["tuning"]})
     khash = _kernel_hash()
     traffic = _traffic_for(khash, layouts[0]) if len(set(layouts)) == 1 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_pairs, "unit": "Gpair/s",

@@ -91,7 +91,11 @@ typedef enum {
                                  on an sm_103 device, else P2P_ERR_UNSUPPORTED */
 } p2p_path;
 
-/* Launch tuning of a plan (the autotuner's knobs).  Zero fields take defaults. */
+/* Launch tuning of a plan (the autotuner's knobs).  Zero fields take defaults.  With
+ * chunk and warps_per_cta both zero (or a NULL tuning) the plan chooses them: 192
+ * sources per item and 8 warps per block, or 256 and 6 when more than half of the
+ * boxes' source lists hold 193 .. 256 sources (a 192-source item would leave each of
+ * them a short tail item of the same fixed cost). */
 typedef struct {
     int32_t chunk;         /* sources staged per work item, multiple of 32, 32..1024 (default 192) */
     int32_t warps_per_cta; /* warps per thread block of the pair kernel, 1..16 (default 8) */

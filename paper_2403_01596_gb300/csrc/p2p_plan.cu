@@ -195,6 +195,8 @@ __global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* _
     padded[b] = (int32_t)((len + 3) & ~3ll);
     atomicMax(&maxes[0], c);
     atomicMax(&maxes[1], own);
+    // lists just over one chunk: a full item plus a short tail item (counted for the default-tuning choice)
+    if (len > chunk && 3 * len <= 4ll * chunk) atomicAdd(&maxes[2], 1);
 }
 
 // Work-item records (unsorted) and their sort keys: larger cost (targets x
@@ -411,8 +413,15 @@ bool tuning_valid(const p2p_tuning& t) {
            t.target_group >= 32 && t.target_group <= 128 && t.target_group % 32 == 0;
 }
 
+// Default launch tuning; a plan whose caller leaves chunk and warps at zero may switch to kWideTuning (see
+// p2p_plan_create).
+constexpr p2p_tuning kDefaultTuning{192, 8, 32, 0};
+constexpr p2p_tuning kWideTuning{256, 6, 32, 0};
+
+bool tuning_is_auto(const p2p_tuning* t) { return !t || (t->chunk == 0 && t->warps_per_cta == 0); }
+
 p2p_tuning resolve_tuning(const p2p_tuning* t) {
-    p2p_tuning r{192, 8, 32, 0};
+    p2p_tuning r = kDefaultTuning;
     if (t) {
         if (t->chunk) r.chunk = t->chunk;
         if (t->warps_per_cta) r.warps_per_cta = t->warps_per_cta;
@@ -684,6 +693,25 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
                                                                      t.chunk, upper, p->box_src, L.list_len,
                                                                      L.n_chunks, L.padded, L.maxes, p->status);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/box_info");
+    if (tuning_is_auto(tuning)) {
+        // When most source lists hold just over one default chunk (193 .. 256 sources), every box would get a
+        // full item and a short tail item with the same fixed cost; 256-source items (6 warps per block, so two
+        // blocks still fit an SM) give those boxes one item each.  The workspace sized for the default chunk
+        // covers the fewer, longer items.
+        int32_t tails = 0;
+        FAIL_CUDA(cudaMemcpyAsync(&tails, L.maxes + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
+        FAIL_CUDA(cudaStreamSynchronize(s), "p2p_plan_create");
+        if (2ll * tails > num_boxes) {
+            t.chunk = kWideTuning.chunk;
+            t.warps_per_cta = kWideTuning.warps_per_cta;
+            p->tune = t;
+            FAIL_CUDA(cudaMemsetAsync(L.maxes, 0, 4 * sizeof(int32_t), s), "p2p_plan_create");
+            k_box_info<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(box_ptr, nbr_ptr, nbr_idx, num_boxes, nnz,
+                                                                             t.chunk, upper, p->box_src, L.list_len,
+                                                                             L.n_chunks, L.padded, L.maxes, p->status);
+            FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/box_info");
+        }
+    }
     FAIL_CUDA(scan_exclusive_i32(L.n_chunks, L.item_off, num_boxes, L.small, L.scan_ws, s), "p2p_plan_create/scan");
     FAIL_CUDA(scan_exclusive_i32(L.padded, p->pk_off, num_boxes, p->pk_off + num_boxes, L.scan_ws, s),
               "p2p_plan_create/scan_lists");
