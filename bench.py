@@ -430,8 +430,8 @@ def run_ours(args):
 
     def one_apply(i, evs=None):
         p = plans[i]
-        if evs:
-            evs[0].record(stream)
+        if evs and i == 0:
+            evs[0].record(stream)  # later occupancies start at the previous one's end event
         C.p2p_apply_stage(p._plan, lams[i], 1, 1, path, stream)
         if evs:
             evs[1].record(stream)
@@ -460,6 +460,8 @@ def run_ours(args):
         flush.zero_()
         for i in range(nd):
             one_apply(i, evs[s][i])
+        for i in range(1, nd):
+            evs[s][i][0] = evs[s][i - 1][2]
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     replicas.barrier()
