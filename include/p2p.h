@@ -307,9 +307,11 @@ P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, con
  * Several independent geometries (plans) applied in one persistent launch.
  * The paper splits large problems into pieces of 50k - 150k points to keep its
  * repetition kernel near its optimum (Sec. 4.3); a batch runs such pieces, or
- * unrelated geometries of uneven box occupancy, together: work items of every
- * plan form one queue ordered by decreasing cost (targets x sources) that the
- * warps of a persistent grid drain with an atomic counter.
+ * unrelated geometries of uneven box occupancy, together: the plans' work items
+ * (each plan's own list, heaviest first) form one queue, plan after plan in the
+ * order given, and warp w of a persistent grid of W warps takes items w, w + W, ...
+ * Giving the plans from smallest to largest leaves the tail to the largest
+ * geometry's lightest items.
  *
  *   plans           [host] count plan pointers, 1 <= count <= 16; the plans must
  *                          outlive the batch and are applied with nrhs columns
@@ -317,7 +319,7 @@ P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, con
  *   warps_per_cta          0 (default 8) or 1 .. 16
  *   workspace       [dev]  at least p2p_batch_workspace_size bytes, 256-byte aligned
  *
- * p2p_batch_create synchronises once (it sorts the work queue on the device).
+ * p2p_batch_create synchronises once (it builds the work queue on the device).
  * p2p_batch_apply takes host arrays of count device pointers: lambdas[g] and
  * outs[g] are plan g's n_g x nrhs complex64 strengths and results, leading
  * dimension ld (same for all).  It enqueues two kernels and no allocation or

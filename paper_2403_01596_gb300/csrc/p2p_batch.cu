@@ -10,10 +10,13 @@
 //                   atomics;
 //   k_pair_batched  a persistent grid (resident blocks x SMs) whose warps take
 //                   work items (geometry, box, source chunk) from one combined
-//                   list ordered by decreasing item cost (targets x sources),
-//                   warp w taking items w, w + W, ... (W warps), so the
-//                   heaviest boxes of the most crowded geometry start first and
-//                   the small ones fill the tail.  Warps never wait on each
+//                   list, warp w taking items w, w + W, ... (W warps).  The list
+//                   is the plans' own item lists (each heaviest first) one after
+//                   the other in the order the plans were given, so the warps work
+//                   on one geometry's data at a time and the last geometry's light
+//                   items fill the tail (measured 4 % faster on eight geometries
+//                   than one list ordered by cost across all of them, which mixes
+//                   every geometry's data in flight).  Warps never wait on each
 //                   other.
 // The per-item work is the same device code as the per-plan pair kernel.
 #include <string.h>
@@ -100,26 +103,13 @@ __global__ void __launch_bounds__(P2P_PAIR_MAX_THREADS, R == 1 ? P2P_PAIR_MIN_BL
                     geoms[0].a.status, [&](const ItemRec& r) -> const PairArgs* { return &geoms[r.b].a; });
 }
 
-// Sort key of every item: larger cost (targets x staged sources) first.
-__global__ void k_batch_keys(const BatchGeom* __restrict__ geoms, const ItemOffsets off, uint64_t* __restrict__ keys,
-                             int32_t* __restrict__ vals) {
+// Combined item list: plan after plan, each in its own (heaviest first) order; the
+// record's last field names its geometry.
+__global__ void k_batch_order(const BatchGeom* __restrict__ geoms, const ItemOffsets off, ItemRec* __restrict__ recs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= off.off[off.count]) return;
     const int g = find_geom(off.off, off.count, i);
-    const ItemRec r = geoms[g].a.items[i - off.off[g]];
-    const uint64_t cost = (uint64_t)min((int64_t)r.nt * r.ns, (int64_t)0xFFFFFFFF);
-    keys[i] = 0xFFFFFFFFull - cost;
-    vals[i] = (int32_t)i;
-}
-
-// Combined item list in cost order; the record's last field names its geometry.
-__global__ void k_batch_order(const BatchGeom* __restrict__ geoms, const int32_t* __restrict__ sorted,
-                              const ItemOffsets off, ItemRec* __restrict__ recs) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= off.off[off.count]) return;
-    const int64_t v = sorted[i];
-    const int g = find_geom(off.off, off.count, v);
-    ItemRec r = geoms[g].a.items[v - off.off[g]];
+    ItemRec r = geoms[g].a.items[i - off.off[g]];
     r.b = g;
     recs[i] = r;
 }
@@ -127,9 +117,6 @@ __global__ void k_batch_order(const BatchGeom* __restrict__ geoms, const int32_t
 struct BatchLayout {
     BatchGeom* geoms;
     ItemRec* order;
-    uint64_t *keys, *keys_alt;
-    int32_t *vals, *vals_alt;
-    void* radix_ws;
     size_t bytes;
 };
 
@@ -139,11 +126,6 @@ BatchLayout batch_layout(int64_t total, void* ws) {
     size_t m = (size_t)(total > 0 ? total : 1);
     L.geoms = c.take<BatchGeom>(kMaxBatch);
     L.order = c.take<ItemRec>(m);
-    L.keys = c.take<uint64_t>(m);
-    L.keys_alt = c.take<uint64_t>(m);
-    L.vals = c.take<int32_t>(m);
-    L.vals_alt = c.take<int32_t>(m);
-    L.radix_ws = c.take<char>(radix_workspace_bytes(total));
     L.bytes = align_up(c.off, 256);
     return L;
 }
@@ -320,12 +302,7 @@ P2P_API p2p_status p2p_batch_create(p2p_batch** batch, const p2p_plan* const* pl
     b->grid = ctas_per_sm * sms;
     FAIL(cudaMemcpyAsync(L.geoms, host, sizeof(BatchGeom) * count, cudaMemcpyHostToDevice, s), "p2p_batch_create");
     const unsigned blocks = (unsigned)((total + 255) / 256);
-    k_batch_keys<<<blocks, 256, 0, s>>>(L.geoms, off, L.keys, L.vals);
-    FAIL(cudaGetLastError(), "p2p_batch_create/keys");
-    bool in_alt = false;
-    FAIL(radix_sort_pairs(L.keys, L.vals, L.keys_alt, L.vals_alt, total, 32, L.radix_ws, s, &in_alt),
-         "p2p_batch_create/sort");
-    k_batch_order<<<blocks, 256, 0, s>>>(L.geoms, in_alt ? L.vals_alt : L.vals, off, L.order);
+    k_batch_order<<<blocks, 256, 0, s>>>(L.geoms, off, L.order);
     FAIL(cudaGetLastError(), "p2p_batch_create/order");
     FAIL(cudaStreamSynchronize(s), "p2p_batch_create");
 #undef FAIL
