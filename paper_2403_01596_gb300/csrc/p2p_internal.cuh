@@ -85,7 +85,6 @@ struct p2p_plan {
     int32_t* nb_src;        // [packed] box-sorted index of every listed source, -1 for padding
     float4* pk_xyz;         // [packed] redundant layout: per-box copy of the listed coordinates
     int32_t* pk_src;        // [packed] redundant layout: original index of every listed source, -1 for padding
-    unsigned long long* queue;  // work-queue counter of the persistent pair kernel
     int32_t grid[3];        // persistent grid of the pair kernel for R = 1, 2, 4 right-hand sides per pass
     int32_t grid_warps[3];  // warps per block of that grid (the tuning's, halved until a block fits)
     float2* lam_buf;        // [max(n, packed) * max_nrhs] sorted / packed strengths

@@ -9,8 +9,9 @@
 // layout (Sec. 3.3) holds a per-box copy of the coordinates and a per-apply
 // repack of the strengths, so a chunk is one contiguous tile.
 //
-// Pipeline.  The kernel is persistent: every warp takes items from a global
-// queue (atomic counter) and keeps two shared-memory stages.  While it sweeps
+// Pipeline.  The kernel is persistent: warp w of W takes items w, w + W, ... of
+// the heaviest-first list (a fixed stride, so the records of the next items can be
+// loaded ahead) and keeps two shared-memory stages.  While it sweeps
 // the targets of item i against stage i % 2, the sources of item i + 1 are
 // already on their way into the other stage -- with cp.async (per-lane 16/8 B
 // asynchronous copies) for the indexed gather, or with one or two TMA bulk

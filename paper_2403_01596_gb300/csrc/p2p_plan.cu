@@ -453,7 +453,6 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, int64_t nnz, p2p_
     const bool red = layout == P2P_LAYOUT_REDUNDANT;
     L.p.status = c.take<unsigned int>(4);
     L.p.scratch64 = c.take<long long>(4);
-    L.p.queue = c.take<unsigned long long>(2);
     L.p.xs = c.take<float4>(m);
     L.p.box_src = c.take<int32_t>(mb);
     L.p.items = c.take<ItemRec>(max_items);
