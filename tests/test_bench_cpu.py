@@ -36,3 +36,18 @@ def test_sample_pairs_fast_with_duplicates_falls_back():
     n = bench._sample_pairs_fast(st, pts, targets)
     assert n == bench._sample_pairs(st, pts, targets)
     assert n == oracle.pair_count(pts, (0.0, 0.0, 0.0), 0.25, 4)
+
+
+def test_oracle_pool_times_shares_and_closes():
+    """Two spawned oracle workers: each rebuilds the seeded sweep workloads, runs its share behind a barrier,
+    and the pool shuts down cleanly."""
+    pool = bench.OraclePool(workers=2)
+    try:
+        assert pool.workers == 2
+        targets = bench._sample_targets(1 << 20, 64, 3)
+        dt = pool.run(3, targets)  # occupancy 64, 32 targets per worker
+        assert 0.0 < dt < 120.0
+        assert all(pr.is_alive() for pr in pool.procs)
+    finally:
+        pool.close()
+    assert not any(pr.is_alive() for pr in pool.procs)
