@@ -159,6 +159,23 @@ def test_grad_points(kernel):
     assert err <= 1e-4, err
 
 
+@pytest.mark.parametrize("layout,nrhs,tuning", [("indexed", 1, None), ("redundant", 1, None),
+                                                 ("indexed", 1, {"chunk": 64, "warps_per_cta": 4}),
+                                                 ("redundant", 3, None), ("indexed", 2, {"chunk": 64})])
+def test_grad_points_layouts_rhs_and_chunks(layout, nrhs, tuning):
+    """Both layouts' box lists, one and several right-hand sides (summed as the oracle does), and boxes split
+    over several items when the chunk is short (their partial gradients meet in the atomic output)."""
+    api = _cuda()
+    wl = W.Workload("grad_ell", W.ellipsoid_211(12000, 17), (-2.0, -2.0, -2.0), 4.0 / 30, 30, 9.0, 17)
+    lam = W.strengths(wl.n, nrhs, 18).reshape(wl.n, nrhs)
+    g = W.strengths(wl.n, nrhs, 19).reshape(wl.n, nrhs)
+    plan = _plan(api, wl, "helmholtz", layout, max_nrhs=nrhs, tuning=tuning)
+    gx = plan.grad_points(torch.from_numpy(lam).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
+    assert plan.async_status() == 0
+    ref = oracle.grad_points(wl.points, lam, g, wl.lo, wl.h, wl.ng, wl.k)
+    assert np.linalg.norm(gx - ref) / np.linalg.norm(ref) <= 1e-4
+
+
 def test_autograd_function():
     api = _cuda()
     wl = _small_sphere(8000, 20, 14)
