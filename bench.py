@@ -16,6 +16,15 @@ between timed steps, outside the timed events.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--layout auto|indexed|redundant]
 
+After the timed steps (outside them) the default run adds two sub-records to
+its line: `redundant` -- the same sweep through the redundant layout of Sec.
+3.3 (per-occupancy repack and pair-kernel times, the pair kernel against the
+MUFU roofline, and the apply against its binding term, HBM or MUFU) -- and
+`multirhs` -- the 2:1:1 ellipsoid (2^21 points, 64 right-hand sides): the
+tensor-core path against the per-RHS and shared-G FP32 paths, rel-L2 per RHS
+against the FP64 oracle on sampled targets, and the tensor-core kernel's
+roofline fraction.  --no-extras skips them.
+
 --impl reference times the FP64 CPU oracle, as it stands, on a bounded sample
 of targets of the same workload (no GPU use).  Under torchrun each rank runs
 an independent replica (the operator has no exchange step on one GPU per
@@ -265,8 +274,11 @@ def cpu_oracle_sample(wls, structs, seconds_per_density: float, seed: int):
         ref = oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, wl.k)
         dt = time.perf_counter() - t
         pairs = _sample_pairs(st, wl.points, targets)
+        # sum of the terms' magnitudes per target: |exp(ikr)| = 1, so the Laplace sum of |lambda| (not timed)
+        abs_sum = oracle.p2p_targets(wl.points, np.abs(lam).astype(np.float64), targets, wl.lo, wl.h, wl.ng, 0.0,
+                                     kernel=oracle.LAPLACE).real
         res.append({"occupancy": wl.meta["target_occupancy"], "targets": targets, "ref": ref, "seconds": dt,
-                    "pairs": pairs, "calib": (fixed, per_target)})
+                    "pairs": pairs, "calib": (fixed, per_target), "abs_sum": abs_sum})
     return res
 
 
@@ -519,6 +531,13 @@ def run_ours(args):
                 "peak_at_measured_clock": (sms * 16 * clk["sm_mhz"] * 1e6 / 3 / 1e9) if clk.get("sm_mhz") else None,
                 "per_occupancy": detail}
 
+    # ---------------- the two layout / precision comparisons, as sub-records (rank 0, N = 1)
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras["redundant"] = measure_redundant(wls, pts, [p.structure for p in plans], pairs, args.extra_steps,
+                                                flush, peaks, sms)
+        extras["multirhs"] = measure_multirhs(1.0, args.extra_steps, args.samples)
+
     # ---------------- CPU oracle baseline and sampled accuracy (rank 0, N = 1)
     cpu = None
     err = None
@@ -538,11 +557,17 @@ def run_ours(args):
                                  "sample": "FP64 oracle on " + ", ".join(
                                      f"{len(r['targets'])} targets at occupancy {r['occupancy']}" for r in res)
                                            + f" ({cpu_pairs} pairs, {cpu_s:.1f} s)"}}
-        errs = []
+        errs, relmax, normwise = [], [], []
         for r, out in zip(res, outs):
             got = out.cpu().numpy()[r["targets"]]
             errs.append(float(np.linalg.norm(got - r["ref"]) / np.linalg.norm(r["ref"])))
-        err = {"rel_l2_max": max(errs), "per_occupancy": errs, "sample": "targets of the cpu_baseline sample",
+            d = np.abs(got - r["ref"])
+            relmax.append(float((d / np.abs(r["ref"])).max()))
+            normwise.append(float((d / r["abs_sum"]).max()))
+        err = {"rel_l2_max": max(errs), "per_occupancy": errs,
+               "max_per_target_rel": relmax,
+               "max_per_target_err_over_abs_sum": normwise,
+               "sample": "targets of the cpu_baseline sample; abs_sum = sum_j |G(r_ij) lambda_j| (oracle)",
                "tolerance": 1e-5}
 
     if rank == 0:
@@ -556,7 +581,7 @@ def run_ours(args):
                     "api": "p2p_apply_host (api.HostPipe), page-locked host buffers",
                     "max_rel_diff_vs_device_apply": e2e_check},
             "gpu_launches": 2 * nd * args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, **extras,
             "wall_s_timed_region": wall, "device": props.name, "sms": sms,
         }
         print(json.dumps(line))
@@ -601,13 +626,17 @@ def _rel_l2_cols(x, ref):
     return np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0)
 
 
-def run_multirhs(args):
+def measure_multirhs(scale, steps, samples, free_first=()):
+    """The 64-RHS comparison on the 2:1:1 ellipsoid (2^21 points, 188^3 grid, leaf edge 0.2 wavelength):
+    the tensor-core path (BF16 hi/lo split, tcgen05, FP32 accumulation) against the FP32 path with G shared
+    over RHS blocks and the plain per-RHS FP32 path, each timed with CUDA events; rel-L2 vs the FP64 oracle
+    per right-hand side on `samples` sampled targets.  Returns the record (timings, errors, roofline)."""
     import torch
+    from paper_2403_01596_gb300 import _capi as C
     from paper_2403_01596_gb300 import api, workloads as W
-    torch.cuda.set_device(0)
     peaks = _peaks()
-    props = torch.cuda.get_device_properties(0)
-    wl = W.ellipsoid_multirhs(int((1 << 21) * args.scale))
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    wl = W.ellipsoid_multirhs(int((1 << 21) * scale))
     nrhs = 64
     pts = torch.from_numpy(wl.points).cuda()
     plan = api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k, max_nrhs=nrhs)
@@ -617,14 +646,13 @@ def run_multirhs(args):
     P = plan.pair_count()
     stream = torch.cuda.current_stream()
     res = {}
-    for path, steps in (("tc_bf16x3", args.ext_steps), ("fp32_shared", max(2, args.ext_steps // 4)),
-                        ("fp32_per_rhs", max(2, args.ext_steps // 8))):
-        med, _ = _events_time(lambda: plan.apply(lam, out=out, path=path), steps, 2, stream)
-        res[path] = {"ms": med, "gpair_rhs_s": P * nrhs / med / 1e6, "out": out.cpu().numpy()}
+    for path, n_steps in (("tc_bf16x3", steps), ("fp32_shared", max(2, steps // 4)),
+                          ("fp32_per_rhs", max(2, steps // 8))):
+        med, _ = _events_time(lambda: plan.apply(lam, out=out, path=path), n_steps, 2, stream)
+        res[path] = {"ms": med, "gpair_rhs_s": P * nrhs / med / 1e6, "steps": n_steps, "out": out.cpu().numpy()}
     # tensor-core path in two phases: strength pre-pack (k_tc_pack), then the pipelined kernel (k_p2p_tc)
-    from paper_2403_01596_gb300 import _capi as C
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.ext_steps)]
-    for i in range(2 + args.ext_steps):
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for i in range(2 + steps):
         e = evs[i - 2] if i >= 2 else None
         if e:
             e[0].record(stream)
@@ -635,14 +663,16 @@ def run_multirhs(args):
         if e:
             e[2].record(stream)
     torch.cuda.synchronize()
+    status = plan.async_status()
     pack_ms = statistics.median(e[0].elapsed_time(e[1]) for e in evs)
     kern_ms = statistics.median(e[1].elapsed_time(e[2]) for e in evs)
-    targets = _sample_targets(wl.n, args.samples, 5)
+    targets = _sample_targets(wl.n, samples, 5)
     ref, cpu_s = _oracle_sampled(wl, lam_np, targets)
     for path in res:
         e = _rel_l2_cols(res[path].pop("out")[targets], ref)
         res[path]["rel_l2_max"] = float(e.max())
         res[path]["rel_l2_per_rhs_mean"] = float(e.mean())
+        res[path]["rel_l2_per_rhs"] = [float(v) for v in e]
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     mufu_peak = props.multi_processor_count * 16 * f_max / 3 / 1e9        # G evaluations per second (G/s)
     tc_flops = 3 * 8 * P * nrhs                                           # hi.hi + hi.lo + lo.hi, realified complex
@@ -651,26 +681,99 @@ def run_multirhs(args):
     groups = int(((sizes + 15) // 16).sum().item())                      # 16-source groups of the pre-pack
     record = ((nrhs + 63) // 64) * 8192 + 16 * 16                        # BF16 hi/lo images + coordinates
     pack_bytes = wl.n * (nrhs * 8 + 16) + groups * record                 # strengths, coordinates read; records written
+    rec = {"workload": "ellipsoid211_multirhs", "n_points": wl.n, "grid": wl.ng, "nrhs": nrhs, "pairs": P,
+           "boxes": plan.num_boxes, "paths": res, "async_status": status,
+           "speedup_tc_vs_fp32_per_rhs": res["fp32_per_rhs"]["ms"] / res["tc_bf16x3"]["ms"],
+           "speedup_tc_vs_fp32_shared": res["fp32_shared"]["ms"] / res["tc_bf16x3"]["ms"],
+           "tolerance": 1e-5,
+           "roofline": {"bound": "alu", "kernel": "k_p2p_tc", "achieved": P / t_tc / 1e9, "peak": mufu_peak,
+                        "unit": "G pair-evaluations/s", "frac": P / t_tc / 1e9 / mufu_peak,
+                        "kernel_ms": kern_ms,
+                        "tensor_tflops": tc_flops / t_tc / 1e12,
+                        "tensor_frac_of_bf16_peak": tc_flops / t_tc / 1e12 / float(peaks["bf16_tflops"]),
+                        "pack": {"kernel": "k_tc_pack", "ms": pack_ms, "bytes": pack_bytes,
+                                 "gbs": pack_bytes / (pack_ms * 1e-3) / 1e9,
+                                 "frac_of_hbm": pack_bytes / (pack_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"])}},
+           "oracle_sample": {"targets": len(targets), "seconds": cpu_s}}
+    del plan, lam, out, pts
+    torch.cuda.empty_cache()
+    return rec
+
+
+def measure_redundant(wls, pts, structures, pairs, steps, flush, peaks, sms):
+    """The redundant layout (Sec. 3.3: per-box copies of each neighbourhood's coordinates, strengths repacked
+    every apply) on the occupancy sweep: per occupancy the repack and pair-kernel times (CUDA events, L2
+    flushed before each apply), the apply rate, the pair kernel against R_MUFU, and the binding term of the
+    whole apply: max(P / R_MUFU, bytes / HBM) with bytes = packed (16 + 8) + n (8 + 8) for the pair kernel and
+    packed (4 + 8 + 8) for the repack."""
+    import torch
+    from paper_2403_01596_gb300 import _capi as C
+    from paper_2403_01596_gb300 import api, workloads as W
+    stream = torch.cuda.current_stream()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    r_mufu = sms * MUFU_LANES_PER_SM_CLK * f_max / MUFU_PER_PAIR["helmholtz"]
+    hbm = float(peaks["hbm_gbs"]) * 1e9
+    path = C.P2P_PATH_FP32_SHARED
+    rows = []
+    for wl, st, P in zip(wls, structures, pairs):
+        plan = api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k, layout="redundant", structure=st)
+        lam = torch.from_numpy(W.strengths(wl.n, 1, wl.seed)).to(pts.device)
+        out = torch.empty_like(lam)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        for i in range(3 + steps):
+            flush.zero_()
+            e = evs[i - 3] if i >= 3 else None
+            if e:
+                e[0].record(stream)
+            C.p2p_apply_stage(plan._plan, lam, 1, 1, path, stream)
+            if e:
+                e[1].record(stream)
+            C.p2p_apply_staged(plan._plan, out, 1, 1, 0, path, stream)
+            if e:
+                e[2].record(stream)
+        torch.cuda.synchronize()
+        stage_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+        pair_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+        packed = int(st.sources)  # sum over boxes of the sources in each neighbourhood (the per-box copies)
+        kbytes = packed * (16 + 8) + wl.n * (8 + 8)
+        rbytes = packed * (4 + 8 + 8)
+        t_mufu, t_hbm = P / r_mufu, (kbytes + rbytes) / hbm
+        t_apply = (stage_ms + pair_ms) * 1e-3
+        rows.append({"occupancy": wl.meta["target_occupancy"], "pairs": P, "packed": packed,
+                     "repack_ms": stage_ms, "pair_kernel_ms": pair_ms, "apply_gpair_s": P / t_apply / 1e9,
+                     "pair_kernel_frac_of_mufu": P / (pair_ms * 1e-3) / r_mufu,
+                     "binding": "hbm" if t_hbm > t_mufu else "mufu",
+                     "binding_us": 1e6 * max(t_mufu, t_hbm), "mufu_us": 1e6 * t_mufu, "hbm_us": 1e6 * t_hbm,
+                     "apply_frac_of_binding": max(t_mufu, t_hbm) / t_apply,
+                     "async_status": plan.async_status(), "tuning": plan.info["tuning"]})
+        del plan
+    tot_p = sum(r["pairs"] for r in rows)
+    tot_ms = sum(r["repack_ms"] + r["pair_kernel_ms"] for r in rows)
+    tot_k = sum(r["pair_kernel_ms"] for r in rows)
+    return {"layout": "redundant", "steps": steps, "apply_gpair_s": tot_p / tot_ms / 1e6,
+            "pair_kernel_frac_of_mufu": tot_p / (tot_k * 1e-3) / r_mufu, "per_occupancy": rows,
+            "l2": "flushed before every apply"}
+
+
+def run_multirhs(args):
+    import torch
+    torch.cuda.set_device(0)
+    rec = measure_multirhs(args.scale, args.ext_steps, args.samples)
+    res = rec["paths"]
     line = {"metric": METRIC + " [64-RHS: pair x RHS]", "value": res["tc_bf16x3"]["gpair_rhs_s"], "unit": UNIT,
             "n_gpus": 1, "steps": args.ext_steps, "warmup": 2, "ms_per_step": res["tc_bf16x3"]["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/f32",
             "data": "synthetic",
-            "config": {"workload": "ellipsoid211_multirhs", "n_points": wl.n, "grid": wl.ng, "nrhs": nrhs,
-                       "pairs": P, "boxes": plan.num_boxes},
+            "config": {k: rec[k] for k in ("workload", "n_points", "grid", "nrhs", "pairs", "boxes")},
             "paths": res,
-            "speedup_tc_vs_fp32_per_rhs": res["fp32_per_rhs"]["ms"] / res["tc_bf16x3"]["ms"],
-            "speedup_tc_vs_fp32_shared": res["fp32_shared"]["ms"] / res["tc_bf16x3"]["ms"],
-            "roofline": {"bound": "alu", "kernel": "k_p2p_tc", "achieved": P / t_tc / 1e9, "peak": mufu_peak,
-                         "unit": "G pair-evaluations/s", "frac": P / t_tc / 1e9 / mufu_peak,
-                         "kernel_ms": kern_ms,
-                         "tensor_tflops": tc_flops / t_tc / 1e12,
-                         "tensor_frac_of_bf16_peak": tc_flops / t_tc / 1e12 / float(peaks["bf16_tflops"]),
-                         "pack": {"kernel": "k_tc_pack", "ms": pack_ms, "bytes": pack_bytes,
-                                  "gbs": pack_bytes / (pack_ms * 1e-3) / 1e9,
-                                  "frac_of_hbm": pack_bytes / (pack_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"])}},
-            "cpu_baseline": {"value": len(targets) * nrhs * (P / wl.n) / cpu_s / 1e9, "unit": UNIT, "cores": 1,
-                             "kind": "oracle", "sample": f"{len(targets)} targets x {nrhs} RHS (pairs estimated "
-                                                         f"from the mean neighbourhood), {cpu_s:.1f} s"}}
+            "speedup_tc_vs_fp32_per_rhs": rec["speedup_tc_vs_fp32_per_rhs"],
+            "speedup_tc_vs_fp32_shared": rec["speedup_tc_vs_fp32_shared"],
+            "roofline": rec["roofline"],
+            "cpu_baseline": {"value": rec["oracle_sample"]["targets"] * rec["nrhs"] * (rec["pairs"] / rec["n_points"])
+                             / rec["oracle_sample"]["seconds"] / 1e9, "unit": UNIT, "cores": 1,
+                             "kind": "oracle", "sample": f"{rec['oracle_sample']['targets']} targets x {rec['nrhs']} "
+                                                         "RHS (pairs estimated from the mean neighbourhood), "
+                                                         f"{rec['oracle_sample']['seconds']:.1f} s"}}
     print(json.dumps(line))
     return 0
 
@@ -846,6 +949,9 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="point-count scale of the extension workloads")
     ap.add_argument("--ext-steps", type=int, default=20)
     ap.add_argument("--samples", type=int, default=400, help="oracle-checked targets of the extension workloads")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the redundant-layout and 64-RHS sub-records of the default run")
+    ap.add_argument("--extra-steps", type=int, default=10, help="timed applies of each sub-record measurement")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: warmup raised to 3 (timing rule)", file=sys.stderr)

@@ -152,10 +152,10 @@ P2P_API p2p_status p2p_bin_points(const float* pts, int64_t n, const double lo[3
 /*
  * Allocation-free variant of p2p_bin_points.  The paper has no counterpart;
  * this entry point exists for callers that cannot allocate device memory when
- * they bin points: code running while a stream is captured into a CUDA graph
- * (an allocation there is not part of the graph and can break the capture),
- * real-time or embedded hosts that fix their device memory budget up front,
- * and plug-ins whose host application owns every allocation.
+ * they bin points: real-time or embedded hosts that fix their device memory
+ * budget up front and refuse allocations afterwards, and plug-ins whose host
+ * application owns every allocation and forbids device allocations from inside
+ * a callback.
  *
  * Inputs, outputs and results are those of p2p_bin_points; there is no work
  * argument.  The scratch lives in one fixed device array inside the library,
@@ -166,11 +166,14 @@ P2P_API p2p_status p2p_bin_points(const float* pts, int64_t n, const double lo[3
  *
  * The first call on a device looks up the array's device address (with that
  * device current) and keeps it; make that first call before any stream
- * capture.  All calls on a device share the array, which keeps the previous
- * call's contents (the call clears what it needs zeroed): calls that overlap
- * on the GPU -- on different streams, or from different host threads on the
- * same device -- race on it and must be serialised by the caller.
- * Synchronises, as p2p_bin_points does.
+ * capture begins.  The kept address belongs to the device's current context:
+ * after cudaDeviceReset (or any other teardown of the primary context) it is
+ * stale, and the next call must not be made in that process.  All calls on a
+ * device share the array, which keeps the previous call's contents (the call
+ * clears what it needs zeroed): calls that overlap on the GPU -- on different
+ * streams, or from different host threads on the same device -- race on it and
+ * must be serialised by the caller.  Like p2p_bin_points, the call
+ * synchronises `stream` before it returns (it reads the box count back).
  */
 #define P2P_BIN_STATIC_MAX_POINTS 65536
 P2P_API p2p_status p2p_bin_points_static(const float* pts, int64_t n, const double lo[3], double h, int32_t ng,
@@ -394,12 +397,6 @@ P2P_API p2p_status p2p_host_pipe_destroy(p2p_host_pipe* pipe);
  */
 P2P_API p2p_status p2p_diag_tc_gemm(const float* A, const float* B, float* D, int32_t K, int32_t n,
                                     unsigned int* status, p2p_stream_t stream);
-/* The same product with A's hi and lo slices written to tensor memory (row m in
- * lane m, K elements packed two per 32-bit column) and read from there by the
- * MMAs, the operand path of the multi-RHS kernel's strengths.  Same arguments. */
-P2P_API p2p_status p2p_diag_tc_gemm_tmem_a(const float* A, const float* B, float* D, int32_t K, int32_t n,
-                                           unsigned int* status, p2p_stream_t stream);
-
 /*
  * Self-check of the bounded waits (not part of the operator): one warp waits
  * on an mbarrier that nothing arrives at, with the poll loop of the pipelined

@@ -91,7 +91,6 @@ def load(build_if_missing: bool = True):
             "p2p_grad_points": ([P, P, P, P, i32, i64, P], ctypes.c_int),
             "p2p_last_async_status": ([P, P], ctypes.c_int),
             "p2p_diag_tc_gemm": ([P, P, P, i32, i32, P, P], ctypes.c_int),
-            "p2p_diag_tc_gemm_tmem_a": ([P, P, P, i32, i32, P, P], ctypes.c_int),
             "p2p_diag_wait_timeout": ([P, i32, P], ctypes.c_int),
             "p2p_batch_workspace_size": ([P, i32, i32, PSZ], ctypes.c_int),
             "p2p_batch_create": ([ctypes.POINTER(P), P, i32, i32, i32, P, sz, P], ctypes.c_int),
@@ -255,9 +254,8 @@ def p2p_last_async_status(plan, stream=None) -> int:
     return load().p2p_last_async_status(plan, _stream(stream))
 
 
-def p2p_diag_tc_gemm(A, B, D, status, stream=None, a_in_tmem=False):
-    f = load().p2p_diag_tc_gemm_tmem_a if a_in_tmem else load().p2p_diag_tc_gemm
-    check(f(_ptr(A), _ptr(B), _ptr(D), int(A.shape[1]), int(B.shape[0]), _ptr(status), _stream(stream)),
+def p2p_diag_tc_gemm(A, B, D, status, stream=None):
+    check(load().p2p_diag_tc_gemm(_ptr(A), _ptr(B), _ptr(D), int(A.shape[1]), int(B.shape[0]), _ptr(status), _stream(stream)),
           "p2p_diag_tc_gemm")
 
 

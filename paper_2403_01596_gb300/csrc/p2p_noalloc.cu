@@ -2,13 +2,12 @@
 // device array instead of a caller-provided workspace.
 //
 // Some callers cannot call cudaMalloc (or any allocator) at the point where
-// they need to bin points: code that runs while a stream is being captured
-// into a CUDA graph (an allocation there is not captured and can invalidate
-// the capture), real-time or embedded hosts that fix their whole device
-// memory budget up front, and plug-ins whose host application owns the
-// allocator and forbids device allocations from inside a callback.  For
-// them p2p_bin_points_static takes the same inputs and outputs as
-// p2p_bin_points but runs its sort and scan in the array below.
+// they need to bin points: real-time or embedded hosts that fix their whole
+// device memory budget up front, and plug-ins whose host application owns the
+// allocator and forbids device allocations from inside a callback.  For them
+// p2p_bin_points_static takes the same inputs and outputs as p2p_bin_points
+// but runs its sort and scan in the array below.  Like p2p_bin_points it
+// synchronises the stream before returning (it reads the box count back).
 //
 // The array holds the scratch of P2P_BIN_STATIC_MAX_POINTS points (about
 // 2 MiB).  It is a file-scope __device__ variable, so every GPU that loads
@@ -16,10 +15,12 @@
 // array's name to a kernel (on the host the name is only a stand-in for the
 // device symbol), so the first call on each device looks up its device
 // address with cudaGetSymbolAddress while that device is current and keeps
-// it.  All calls on a device share the one array and it keeps the previous
-// call's contents; the binning clears everything it needs zeroed.  Calls
-// that overlap on the GPU (different streams, or different host threads on
-// the same device) race on the array and must be serialised by the caller.
+// it; a teardown of the device's primary context (cudaDeviceReset) makes the
+// kept address stale.  All calls on a device share the one array and it keeps
+// the previous call's contents; the binning clears everything it needs
+// zeroed.  Calls that overlap on the GPU (different streams, or different
+// host threads on the same device) race on the array and must be serialised
+// by the caller.
 #include <mutex>
 
 #include "p2p_internal.cuh"

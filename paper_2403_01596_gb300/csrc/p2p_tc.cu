@@ -156,17 +156,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         : "memory");
 }
 
-// The same MMA with A read from tensor memory: row m of A in TMEM lane m, its 16 K elements packed two per
-// 32-bit column (even k in the low half) in the 8 columns starting at a_tmem.
-__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -201,14 +190,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-// Registers into 32 lanes x 8 consecutive 32-bit columns of TMEM (the warp's lane quadrant).
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(r[0]),
-                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // 32 lanes x 16 consecutive 32-bit columns of TMEM into registers.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -790,10 +771,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ 
 
 // D[128 x N] = A[128 x K] . B[N x K]^T with A, B split into BF16 hi + lo (3 MMAs
 // per 16-wide K slice), through the same operand layout, descriptors and
-// instruction descriptor as k_p2p_tc.  A_TMEM: A's hi and lo slices go to tensor
-// memory (thread m writes row m into its warp's lane quadrant) and the MMAs read
-// A from there.
-template <bool A_TMEM>
+// instruction descriptor as k_p2p_tc.
 __global__ void __launch_bounds__(128, 1) k_tc_gemm_check(const float* __restrict__ A, const float* __restrict__ B,
                                                           float* __restrict__ D, int K, int n, int tmem_cols,
                                                           unsigned int* __restrict__ status) {
@@ -816,25 +794,13 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm_check(const float* __restric
     const uint32_t tmem = *slot;
     const uint32_t idesc = idesc_bf16_f32(n);
     bool ok = true;
-    const uint32_t a_col = (uint32_t)tmem_cols - 16u;  // A hi: 8 columns, then A lo: 8 columns
     for (int ks = 0; ks < K / kSrcGroup && ok; ++ks) {
-        if (A_TMEM) {
-            uint32_t hi[8], lo[8];
+        for (int c = tid; c < 128 * 2; c += 128) {
+            const int row = c >> 1, half = c & 1;
+            float v[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                split2(A[(int64_t)tid * K + ks * 16 + 2 * j], A[(int64_t)tid * K + ks * 16 + 2 * j + 1], hi[j], lo[j]);
-            const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16) + a_col;
-            tmem_st8(row_addr, hi);
-            tmem_st8(row_addr + 8u, lo);
-            tmem_wait_st();
-        } else {
-            for (int c = tid; c < 128 * 2; c += 128) {
-                const int row = c >> 1, half = c & 1;
-                float v[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] = A[(int64_t)row * K + ks * 16 + half * 8 + i];
-                store_split<8>(a_hi, a_lo, op_off(row, half * 8), v);
-            }
+            for (int i = 0; i < 8; ++i) v[i] = A[(int64_t)row * K + ks * 16 + half * 8 + i];
+            store_split<8>(a_hi, a_lo, op_off(row, half * 8), v);
         }
         for (int c = tid; c < n * 2; c += 128) {
             const int row = c >> 1, half = c & 1;
@@ -848,15 +814,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm_check(const float* __restric
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            if (A_TMEM) {
-                mma_bf16_ta(tmem, tmem + a_col, smem_desc(smem_u32(b_hi)), idesc, ks == 0 ? 0u : 1u);
-                mma_bf16_ta(tmem, tmem + a_col, smem_desc(smem_u32(b_lo)), idesc, 1u);
-                mma_bf16_ta(tmem, tmem + a_col + 8u, smem_desc(smem_u32(b_hi)), idesc, 1u);
-            } else {
-                mma_bf16(tmem, smem_desc(smem_u32(a_hi)), smem_desc(smem_u32(b_hi)), idesc, ks == 0 ? 0u : 1u);
-                mma_bf16(tmem, smem_desc(smem_u32(a_hi)), smem_desc(smem_u32(b_lo)), idesc, 1u);
-                mma_bf16(tmem, smem_desc(smem_u32(a_lo)), smem_desc(smem_u32(b_hi)), idesc, 1u);
-            }
+            mma_bf16(tmem, smem_desc(smem_u32(a_hi)), smem_desc(smem_u32(b_hi)), idesc, ks == 0 ? 0u : 1u);
+            mma_bf16(tmem, smem_desc(smem_u32(a_hi)), smem_desc(smem_u32(b_lo)), idesc, 1u);
+            mma_bf16(tmem, smem_desc(smem_u32(a_lo)), smem_desc(smem_u32(b_hi)), idesc, 1u);
             mma_commit(bar);
         }
         // the operands are rewritten next slice: wait for these MMAs
@@ -980,27 +940,14 @@ p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t
     return P2P_OK;
 }
 
-namespace {
-p2p_status diag_gemm(const float* A, const float* B, float* D, int32_t K, int32_t n, unsigned int* status,
-                     cudaStream_t s, bool a_tmem) {
+extern "C" P2P_API p2p_status p2p_diag_tc_gemm(const float* A, const float* B, float* D, int32_t K, int32_t n,
+                                               unsigned int* status, p2p_stream_t stream) {
     if (!A || !B || !D || !status || K < 16 || K % 16 != 0 || n < 16 || n > 256 || n % 16 != 0)
         return P2P_ERR_INVALID;
     const int smem = kImage + 2 * (n / 8) * kSbo + 64;
-    auto kern = a_tmem ? k_tc_gemm_check<true> : k_tc_gemm_check<false>;
-    P2P_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "p2p_diag_tc_gemm");
-    // D in columns [0, n), A's hi and lo slices in the last 16 columns of the allocation
-    kern<<<1, 128, smem, s>>>(A, B, D, K, n, tmem_cols_for(n + 16), status);
+    P2P_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm_check, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                 "p2p_diag_tc_gemm");
+    k_tc_gemm_check<<<1, 128, smem, (cudaStream_t)stream>>>(A, B, D, K, n, tmem_cols_for(n), status);
     P2P_CHECK_LAUNCH("p2p_diag_tc_gemm");
     return P2P_OK;
-}
-}  // namespace
-
-extern "C" P2P_API p2p_status p2p_diag_tc_gemm(const float* A, const float* B, float* D, int32_t K, int32_t n,
-                                               unsigned int* status, p2p_stream_t stream) {
-    return diag_gemm(A, B, D, K, n, status, (cudaStream_t)stream, false);
-}
-
-extern "C" P2P_API p2p_status p2p_diag_tc_gemm_tmem_a(const float* A, const float* B, float* D, int32_t K, int32_t n,
-                                                      unsigned int* status, p2p_stream_t stream) {
-    return diag_gemm(A, B, D, K, n, status, (cudaStream_t)stream, true);
 }

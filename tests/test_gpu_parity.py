@@ -1,9 +1,15 @@
 """GPU parity of the CUDA path against the FP64 oracle (call through the C ABI).
 
 Tolerances (FP32 kernel vs FP64 oracle): relative L2 error per right-hand
-side <= 1e-5 for potentials; box ids, permutation, box pointers and neighbour
-lists bit-exact.  The coordinate gradient is compared at relative L2 <= 1e-4
-(its terms scale like 1/r^2, one more power of the close-pair dynamic range).
+side <= 1e-5 for potentials and for the coordinate gradient; box ids,
+permutation, box pointers and neighbour lists bit-exact.  Where a test also
+checks targets one by one, the error of target i is measured against
+S_i = sum_j |G(r_ij) lambda_j| (the sum of the magnitudes of its terms, i.e. the
+oracle's Laplace sum of |lambda|, since |exp(ikr)| = 1): an FP32 evaluation
+whose every term is accurate to a few units of 2^-24 has
+|out_i - ref_i| <= c 2^-24 S_i however much the terms cancel, so
+max_i |out_i - ref_i| / S_i <= 2e-6 is asserted and the plain per-target
+maximum relative error is printed beside it.
 """
 import numpy as np
 import pytest
@@ -28,6 +34,17 @@ def rel_l2(x, ref):
     x = np.asarray(x).reshape(ref.shape[0], -1)
     ref = np.asarray(ref).reshape(ref.shape[0], -1)
     return np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+def per_target(out, ref, wl, lam, kernel=None):
+    """(max over targets of |out - ref| / S_i, max over targets of |out - ref| / |ref|), see the docstring."""
+    absl = np.abs(np.asarray(lam)).astype(np.float64)
+    S = oracle.p2p(wl.points, absl, wl.lo, wl.h, wl.ng, 0.0, kernel=oracle.LAPLACE).real
+    S = S.reshape(S.shape[0], -1)
+    d = np.abs(np.asarray(out).reshape(S.shape[0], -1) - np.asarray(ref).reshape(S.shape[0], -1))
+    r = np.abs(np.asarray(ref).reshape(S.shape[0], -1))
+    ok = S > 0
+    return float((d[ok] / S[ok]).max()), float((d[r > 0] / r[r > 0]).max())
 
 
 def _plan(api, wl, kernel="helmholtz", layout="indexed", max_nrhs=1, tuning=None, k=None):
@@ -100,7 +117,31 @@ def test_apply_surfaces(layout, case):
     plan = _plan(api, wl, "helmholtz", layout)
     out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
     ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
-    assert rel_l2(out, ref).max() <= TOL
+    err = rel_l2(out, ref).max()
+    normwise, relmax = per_target(out, ref, wl, lam)
+    print(f"{case} {layout}: rel-L2 {err:.2e}, max |err|/S {normwise:.2e}, max per-target relative {relmax:.2e}")
+    assert err <= TOL
+    assert normwise <= 2e-6
+
+
+@pytest.mark.parametrize("edge", [1.0, 2.0, 4.0])
+@pytest.mark.parametrize("layout", ["indexed", "redundant"])
+def test_apply_high_frequency(edge, layout):
+    """Leaf edges of 1, 2 and 4 wavelengths (k r up to 22, 44 and 87 rad inside a neighbourhood): the FP32
+    phase k * r carries a relative error of a few 2^-24, i.e. an absolute phase error that grows with k r, so
+    the error grows with the leaf size in wavelengths; up to 4 wavelengths it stays within the tolerance."""
+    api = _cuda()
+    n, ng = 24000, 12
+    wl = W.Workload(f"cube_hf{edge}", W.uniform_cube(n, 31), (0.0, 0.0, 0.0), 1.0 / ng, ng, 2 * np.pi * edge * ng, 31)
+    lam = W.strengths(n, 1, 31)
+    plan = _plan(api, wl, "helmholtz", layout)
+    out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
+    ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
+    err = rel_l2(out, ref).max()
+    normwise, relmax = per_target(out, ref, wl, lam)
+    print(f"leaf edge {edge} wavelengths, {layout}: rel-L2 {err:.2e}, max |err|/S {normwise:.2e}, "
+          f"max per-target relative {relmax:.2e}")
+    assert err <= TOL
 
 
 @pytest.mark.parametrize("tuning", [{"chunk": 32, "warps_per_cta": 4, "target_group": 32},
@@ -156,7 +197,8 @@ def test_grad_points(kernel):
     gx = plan.grad_points(torch.from_numpy(lam).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
     ref = oracle.grad_points(wl.points, lam, g, wl.lo, wl.h, wl.ng, k, kernel=kern)
     err = np.linalg.norm(gx - ref) / np.linalg.norm(ref)
-    assert err <= 1e-4, err
+    print(f"coordinate gradient ({kernel}): rel-L2 {err:.3e}")
+    assert err <= TOL, err
 
 
 @pytest.mark.parametrize("layout,nrhs,tuning", [("indexed", 1, None), ("redundant", 1, None),
@@ -173,7 +215,7 @@ def test_grad_points_layouts_rhs_and_chunks(layout, nrhs, tuning):
     gx = plan.grad_points(torch.from_numpy(lam).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
     assert plan.async_status() == 0
     ref = oracle.grad_points(wl.points, lam, g, wl.lo, wl.h, wl.ng, wl.k)
-    assert np.linalg.norm(gx - ref) / np.linalg.norm(ref) <= 1e-4
+    assert np.linalg.norm(gx - ref) / np.linalg.norm(ref) <= TOL
 
 
 def test_autograd_function():
@@ -190,7 +232,7 @@ def test_autograd_function():
     ref_lam = oracle.p2p(wl.points, g.cpu().numpy(), wl.lo, wl.h, wl.ng, wl.k, adjoint=True)
     assert rel_l2(lam.grad.cpu().numpy(), ref_lam).max() <= TOL
     ref_x = oracle.grad_points(wl.points, lam.detach().cpu().numpy(), g.cpu().numpy(), wl.lo, wl.h, wl.ng, wl.k)
-    assert np.linalg.norm(pts.grad.cpu().numpy() - ref_x) / np.linalg.norm(ref_x) <= 1e-4
+    assert np.linalg.norm(pts.grad.cpu().numpy() - ref_x) / np.linalg.norm(ref_x) <= TOL
 
 
 def test_edge_cases():

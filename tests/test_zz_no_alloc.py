@@ -1,9 +1,9 @@
 """The allocation-free binning entry point against the workspace one.
 
 p2p_bin_points_static serves callers that cannot allocate device memory at the
-point where they bin (inside a stream capture, under a fixed memory budget, or
-inside a host application's callback): its scratch is a fixed array inside the
-library.  Two calls in a row, with different point sets, must give exactly the
+point where they bin (under a fixed device-memory budget, or inside a host
+application's callback that forbids allocations): its scratch is a fixed array
+inside the library.  Two calls in a row, with different point sets, must give exactly the
 outputs of p2p_bin_points (integer outputs: bit-exact), so nothing left in the
 shared array by one call leaks into the next.  This file is collected last so
 that a run stopping at the first failure has already run every other test.
