@@ -64,8 +64,12 @@ def _load():
             lib.oracle_p2p_targets.argtypes = [P, i64, P, dbl, i32, cint, dbl, cint, P, i32, P, i64, P]
             lib.oracle_pair_count.argtypes = [P, i64, P, dbl, i32, P]
             lib.oracle_grad_points.argtypes = [P, i64, P, dbl, i32, cint, dbl, P, P, i32, P]
+            lib.oracle_neighbors_st.argtypes = [P, i32, P, i32, i32, P, P]
+            lib.oracle_p2p_st.argtypes = [P, i64, P, i64, P, dbl, i32, cint, dbl, cint, P, i32, P]
+            lib.oracle_p2p_st_targets.argtypes = [P, i64, P, i64, P, dbl, i32, cint, dbl, cint, P, i32, P, i64, P]
             for f in ("oracle_morton_key", "oracle_point_cells", "oracle_bin", "oracle_neighbors",
-                      "oracle_p2p", "oracle_p2p_targets", "oracle_pair_count", "oracle_grad_points"):
+                      "oracle_p2p", "oracle_p2p_targets", "oracle_pair_count", "oracle_grad_points",
+                      "oracle_neighbors_st", "oracle_p2p_st", "oracle_p2p_st_targets"):
                 getattr(lib, f).restype = cint
             _lib = lib
     return _lib
@@ -185,3 +189,46 @@ def grad_points(points, lam, g, lo, h: float, ng: int, k: float, kernel: int = H
     _check(_load().oracle_grad_points(_ptr(p), n, _ptr(_lo(lo)), h, ng, kernel, k, _ptr(l64), _ptr(g64),
                                       nrhs, _ptr(grad)), "grad_points")
     return grad
+
+
+# ---------------------------------------------------- separate point sets --
+
+def neighbors_st(tgt_keys, src_keys, ng: int) -> tuple[np.ndarray, np.ndarray]:
+    """Per target box, the source boxes within Chebyshev cell distance 1 (ascending source box id)."""
+    tk = np.ascontiguousarray(np.asarray(tgt_keys, dtype=np.int64))
+    sk = np.ascontiguousarray(np.asarray(src_keys, dtype=np.int64))
+    B = tk.shape[0]
+    nptr = np.empty(B + 1, dtype=np.int32)
+    nidx = np.empty(max(27 * B, 1), dtype=np.int32)
+    _check(_load().oracle_neighbors_st(_ptr(tk), B, _ptr(sk), sk.shape[0], ng, _ptr(nptr), _ptr(nidx)),
+           "neighbors_st")
+    return nptr, nidx[:nptr[-1]].copy()
+
+
+def p2p_st(targets, sources, lam, lo, h: float, ng: int, k: float, kernel: int = HELMHOLTZ,
+           conj: bool = False) -> np.ndarray:
+    """out (n_tgt[, nrhs]) = A lam with A the near field from the source set to the target set (both binned on
+    one grid); conj=True gives conj(A) lam.  The adjoint A^H g is p2p_st(sources, targets, g, ..., conj=True)."""
+    t = _pts64(targets)
+    s = _pts64(sources)
+    l64, nrhs = _lam64(lam, s.shape[0])
+    out = np.zeros((t.shape[0], nrhs, 2), dtype=np.float64)
+    _check(_load().oracle_p2p_st(_ptr(t), t.shape[0], _ptr(s), s.shape[0], _ptr(_lo(lo)), h, ng, kernel, k,
+                                 int(conj), _ptr(l64), nrhs, _ptr(out)), "p2p_st")
+    res = out[..., 0] + 1j * out[..., 1]
+    return res[:, 0] if np.asarray(lam).ndim == 1 else res
+
+
+def p2p_st_targets(targets, sources, lam, which, lo, h: float, ng: int, k: float, kernel: int = HELMHOLTZ,
+                   conj: bool = False) -> np.ndarray:
+    """p2p_st for the selected target indices `which` only."""
+    t = _pts64(targets)
+    s = _pts64(sources)
+    l64, nrhs = _lam64(lam, s.shape[0])
+    w = np.ascontiguousarray(np.asarray(which, dtype=np.int64))
+    out = np.zeros((w.shape[0], nrhs, 2), dtype=np.float64)
+    _check(_load().oracle_p2p_st_targets(_ptr(t), t.shape[0], _ptr(s), s.shape[0], _ptr(_lo(lo)), h, ng, kernel,
+                                         k, int(conj), _ptr(l64), nrhs, _ptr(w), w.shape[0], _ptr(out)),
+           "p2p_st_targets")
+    res = out[..., 0] + 1j * out[..., 1]
+    return res[:, 0] if np.asarray(lam).ndim == 1 else res

@@ -23,6 +23,11 @@
  *   Helmholtz:  G(r) = exp(+i k r) / (4 pi r)
  *   Laplace:    G(r) = 1 / (4 pi r)
  *
+ * The same sum between two point sets -- targets x_i and sources y_j binned on
+ * one grid, the neighbours of a target box being the source boxes around its
+ * cell -- is oracle_p2p_st at the end of this file (Sec. 3.1 keeps target and
+ * source coordinates as separate arrays).
+ *
  * The paper's own test kernel is a 2D electric potential whose formula it
  * never prints (Sec. 2 and Sec. 4); the 3D Helmholtz / Laplace kernels and the
  * 27-box neighbourhood (the 3D analogue of the 9 boxes of Sec. 3.2) are the
@@ -409,5 +414,172 @@ int oracle_grad_points(const double* pts, int64_t n, const double lo[3], double 
         for (int a = 0; a < 3; ++a) grad[3 * m + a] = acc[a];
     }
     tree_free(&t);
+    return OK;
+}
+
+/* ------------------------------------------- separate targets and sources --- */
+/*
+ * The paper's tree object keeps target and source coordinates as separate
+ * arrays (Sec. 3.1; Sec. 3.2 lists the target coordinates and the source
+ * coordinates of each box separately).  Here both sets are binned on the same
+ * uniform leaf grid, each with its own Morton-ranked box ids; the neighbours of
+ * target box b are the non-empty SOURCE boxes whose cells lie within Chebyshev
+ * distance 1 of b's cell, ascending source box id; a target and a source at
+ * the same position (r = 0) are skipped, as for one point set.
+ *
+ *   out_i = sum over sources j with cell(j) within distance 1 of cell(i), r_ij > 0, of G(r_ij) lambda_j
+ *
+ * Loop order: target boxes in id order -> targets of the box in sorted order ->
+ * neighbour source boxes ascending -> sources of that box in sorted order.
+ */
+
+/* nbr_ptr: nbt + 1 entries; nbr_idx: up to 27 * nbt entries. */
+int oracle_neighbors_st(const int64_t* tgt_keys, int32_t nbt, const int64_t* src_keys, int32_t nbs, int32_t ng,
+                        int32_t* nbr_ptr, int32_t* nbr_idx) {
+    if (nbt < 0 || nbs < 0 || ng < 1 || ng > (1 << 21)) return ERR_INVALID;
+    int64_t nnz = 0;
+    nbr_ptr[0] = 0;
+    for (int32_t b = 0; b < nbt; ++b) {
+        int64_t c[3];
+        morton_split(tgt_keys[b], c);
+        int32_t found[27];
+        int nf = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= ng || y >= ng || z >= ng) continue;
+                    int32_t id = find_box(src_keys, nbs, morton_interleave(x, y, z));
+                    if (id >= 0) found[nf++] = id;
+                }
+        for (int a = 1; a < nf; ++a) {
+            int32_t v = found[a];
+            int q = a - 1;
+            while (q >= 0 && found[q] > v) {
+                found[q + 1] = found[q];
+                --q;
+            }
+            found[q + 1] = v;
+        }
+        for (int a = 0; a < nf; ++a) nbr_idx[nnz++] = found[a];
+        nbr_ptr[b + 1] = (int32_t)nnz;
+    }
+    return OK;
+}
+
+typedef struct {
+    tree t;     /* targets: binning, point_box, box_keys, box_ptr (nbr_* unused) */
+    tree s;     /* sources: binning */
+    int32_t* nbr_ptr;
+    int32_t* nbr_idx;
+} tree_st;
+
+static void tree_st_free(tree_st* q) {
+    tree_free(&q->t);
+    tree_free(&q->s);
+    free(q->nbr_ptr);
+    free(q->nbr_idx);
+}
+
+static int bin_only(const double* pts, int64_t n, const double lo[3], double h, int32_t ng, tree* t) {
+    memset(t, 0, sizeof(*t));
+    t->n = n;
+    size_t m = (size_t)(n > 0 ? n : 1);
+    t->perm = (int32_t*)malloc(sizeof(int32_t) * m);
+    t->point_box = (int32_t*)malloc(sizeof(int32_t) * m);
+    t->box_keys = (int64_t*)malloc(sizeof(int64_t) * m);
+    t->box_ptr = (int32_t*)malloc(sizeof(int32_t) * (m + 1));
+    if (!t->perm || !t->point_box || !t->box_keys || !t->box_ptr) {
+        tree_free(t);
+        return ERR_ALLOC;
+    }
+    int st = oracle_bin(pts, n, lo, h, ng, t->perm, t->point_box, t->box_keys, t->box_ptr, &t->nb);
+    if (st != OK) tree_free(t);
+    return st;
+}
+
+static int tree_st_build(const double* tgt, int64_t nt, const double* src, int64_t ns, const double lo[3], double h,
+                         int32_t ng, tree_st* q) {
+    memset(q, 0, sizeof(*q));
+    int st = bin_only(tgt, nt, lo, h, ng, &q->t);
+    if (st != OK) return st;
+    st = bin_only(src, ns, lo, h, ng, &q->s);
+    if (st != OK) {
+        tree_free(&q->t);
+        return st;
+    }
+    size_t mb = (size_t)(q->t.nb > 0 ? q->t.nb : 1);
+    q->nbr_ptr = (int32_t*)malloc(sizeof(int32_t) * (mb + 1));
+    q->nbr_idx = (int32_t*)malloc(sizeof(int32_t) * 27 * mb);
+    if (!q->nbr_ptr || !q->nbr_idx) {
+        tree_st_free(q);
+        return ERR_ALLOC;
+    }
+    st = oracle_neighbors_st(q->t.box_keys, q->t.nb, q->s.box_keys, q->s.nb, ng, q->nbr_ptr, q->nbr_idx);
+    if (st != OK) tree_st_free(q);
+    return st;
+}
+
+/* Sum for one target (original index i of the target set) over the sources of its neighbourhood. */
+static void target_sum_st(const tree_st* q, const double* tgt, const double* src, int kernel, double k, int conj,
+                          const double* lam, int32_t nrhs, int64_t i, double* out) {
+    for (int32_t r = 0; r < nrhs; ++r) out[2 * r] = out[2 * r + 1] = 0.0;
+    int32_t b = q->t.point_box[i];
+    const double* xi = tgt + 3 * i;
+    for (int32_t e = q->nbr_ptr[b]; e < q->nbr_ptr[b + 1]; ++e) {
+        int32_t c = q->nbr_idx[e];
+        for (int32_t s = q->s.box_ptr[c]; s < q->s.box_ptr[c + 1]; ++s) {
+            int64_t j = q->s.perm[s];
+            const double* yj = src + 3 * j;
+            double dx = xi[0] - yj[0], dy = xi[1] - yj[1], dz = xi[2] - yj[2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 == 0.0) continue; /* a target at a source's position */
+            double gr, gi;
+            green(kernel, k, conj, sqrt(r2), &gr, &gi);
+            const double* lj = lam + 2 * (size_t)nrhs * (size_t)j;
+            for (int32_t r = 0; r < nrhs; ++r) {
+                double lr = lj[2 * r], li = lj[2 * r + 1];
+                out[2 * r] += gr * lr - gi * li;
+                out[2 * r + 1] += gr * li + gi * lr;
+            }
+        }
+    }
+}
+
+/*
+ * out (nt x nrhs complex, target order) = A lambda with A the nt x ns near-field
+ * operator from the sources to the targets; conj = 1 gives conj(A) lambda.
+ * lam: ns x nrhs complex (source order).  The adjoint A^H g (source space) is
+ * the same call with the roles of the two sets exchanged and conj = 1, since
+ * G(x, y) = G(y, x) and the neighbour relation is symmetric.
+ */
+int oracle_p2p_st(const double* tgt, int64_t nt, const double* src, int64_t ns, const double lo[3], double h,
+                  int32_t ng, int kernel, double k, int conj, const double* lam, int32_t nrhs, double* out) {
+    if (nrhs < 1 || (kernel != K_HELMHOLTZ && kernel != K_LAPLACE)) return ERR_INVALID;
+    tree_st q;
+    int st = tree_st_build(tgt, nt, src, ns, lo, h, ng, &q);
+    if (st != OK) return st;
+    for (int32_t b = 0; b < q.t.nb; ++b)
+        for (int32_t s = q.t.box_ptr[b]; s < q.t.box_ptr[b + 1]; ++s) {
+            int64_t i = q.t.perm[s];
+            target_sum_st(&q, tgt, src, kernel, k, conj, lam, nrhs, i, out + 2 * (size_t)nrhs * (size_t)i);
+        }
+    tree_st_free(&q);
+    return OK;
+}
+
+/* The same sum for a list of targets (original target indices) only; out: count x nrhs complex. */
+int oracle_p2p_st_targets(const double* tgt, int64_t nt, const double* src, int64_t ns, const double lo[3],
+                          double h, int32_t ng, int kernel, double k, int conj, const double* lam, int32_t nrhs,
+                          const int64_t* targets, int64_t count, double* out) {
+    if (nrhs < 1 || (kernel != K_HELMHOLTZ && kernel != K_LAPLACE)) return ERR_INVALID;
+    for (int64_t a = 0; a < count; ++a)
+        if (targets[a] < 0 || targets[a] >= nt) return ERR_INVALID;
+    tree_st q;
+    int st = tree_st_build(tgt, nt, src, ns, lo, h, ng, &q);
+    if (st != OK) return st;
+    for (int64_t a = 0; a < count; ++a)
+        target_sum_st(&q, tgt, src, kernel, k, conj, lam, nrhs, targets[a], out + 2 * (size_t)nrhs * (size_t)a);
+    tree_st_free(&q);
     return OK;
 }

@@ -316,3 +316,96 @@ def test_gradient_finite_differences(oracle_lib):
     q[i, 1] -= 2 * eps
     lm = loss_l(q)
     assert abs((lp - lm) / (2 * eps) - gradl[i, 1]) <= 1e-5 * max(1.0, abs(gradl[i, 1]))
+
+
+# ------------------------------------------------- separate point sets ----
+# Sec. 3.1 keeps target and source coordinates as separate arrays: the same sum
+# between two point sets binned on one grid.
+
+def _brute_st(t, s, lam, lo, h, ng, k, laplace=False, conj=False):
+    """All target-source pairs; neighbour mask = Chebyshev distance of the two cells <= 1."""
+    ct, cs = _cells_numpy(t, lo, h, ng), _cells_numpy(s, lo, h, ng)
+    mask = np.abs(ct[:, None, :] - cs[None, :, :]).max(axis=2) <= 1
+    d = t.astype(np.float64)[:, None, :] - s.astype(np.float64)[None, :, :]
+    r = np.sqrt((d * d).sum(axis=2))
+    valid = mask & (r > 0)
+    rs = np.where(valid, r, 1.0)
+    g = 1.0 / (4 * np.pi * rs) if laplace else np.exp((-1j if conj else 1j) * k * rs) / (4 * np.pi * rs)
+    return np.where(valid, g, 0.0) @ lam
+
+
+@pytest.mark.parametrize("nt,ns,ng,seed", [(700, 1100, 5, 1), (1500, 400, 7, 2), (1, 900, 3, 3), (800, 1, 4, 4)])
+def test_st_matches_bruteforce(oracle_lib, nt, ns, ng, seed):
+    rng = np.random.default_rng(seed)
+    t = rng.random((nt, 3)).astype(np.float32)
+    s = (rng.random((ns, 3)) * 1.1 - 0.05).astype(np.float32)  # some sources outside the grid: clamped
+    s[: min(ns, nt) // 3] = t[: min(ns, nt) // 3]              # shared positions: r = 0 pairs are skipped
+    lam = W.strengths(ns, 2, seed).reshape(ns, 2)
+    lo, h = (0.0, 0.0, 0.0), 1.0 / ng
+    for laplace in (False, True):
+        got = oracle_lib.p2p_st(t, s, lam, lo, h, ng, 7.0, kernel=oracle_lib.LAPLACE if laplace else 0)
+        ref = _brute_st(t, s, lam, lo, h, ng, 7.0, laplace=laplace)
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    got = oracle_lib.p2p_st(t, s, lam, lo, h, ng, 7.0, conj=True)
+    np.testing.assert_allclose(got, _brute_st(t, s, lam, lo, h, ng, 7.0, conj=True), rtol=1e-12,
+                               atol=1e-12 * np.abs(got).max())
+
+
+def test_st_dense_case_and_closed_form(oracle_lib):
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(9)
+    t = rng.random((300, 3)).astype(np.float32)
+    s = rng.random((500, 3)).astype(np.float32)
+    lam = W.strengths(500, 1, 9)
+    k = 5.5
+    r = spatial.distance.cdist(t.astype(np.float64), s.astype(np.float64))
+    A = np.exp(1j * k * r) / (4 * np.pi * r)
+    # ng = 2: every target box neighbours every source box, so the near field is the dense operator
+    got = oracle_lib.p2p_st(t, s, lam, (0, 0, 0), 0.5, 2, k)
+    np.testing.assert_allclose(got, A @ lam, rtol=1e-12, atol=1e-13)
+    # one target, one source at r = 0.5, k = pi: exp(i pi / 2) / (4 pi 0.5) = i / (2 pi)
+    one = oracle_lib.p2p_st(np.array([[0.1, 0.2, 0.3]], np.float32), np.array([[0.1, 0.2, 0.8]], np.float32),
+                            np.array([1.0 + 0j]), (0, 0, 0), 1.0, 1, math.pi)
+    assert abs(one[0] - 1j / (2 * math.pi)) < 1e-15
+
+
+def test_st_reduces_to_one_set_and_reciprocity(oracle_lib):
+    rng = np.random.default_rng(11)
+    p = rng.random((1200, 3)).astype(np.float32)
+    q = rng.random((900, 3)).astype(np.float32)
+    lo, h, ng, k = (0, 0, 0), 1.0 / 6, 6, 9.0
+    lam = W.strengths(1200, 1, 11)
+    # sources = targets: the one-set operator, summed in the same order, bit for bit
+    np.testing.assert_array_equal(oracle_lib.p2p_st(p, p, lam, lo, h, ng, k), oracle_lib.p2p(p, lam, lo, h, ng, k))
+    # G(x, y) = G(y, x) and the cell relation is symmetric: mu^T (A_pq lam) = lam^T (A_qp mu), no conjugation,
+    # and the adjoint A_pq^H = conj(A_qp): <A_pq lam, mu> = <lam, A_qp^conj mu>
+    lam_q = W.strengths(900, 1, 12)
+    mu = W.strengths(1200, 1, 13)
+    a = mu @ oracle_lib.p2p_st(p, q, lam_q, lo, h, ng, k)
+    b = lam_q @ oracle_lib.p2p_st(q, p, mu, lo, h, ng, k)
+    assert abs(a - b) <= 1e-12 * abs(a)
+    lhs = np.vdot(mu, oracle_lib.p2p_st(p, q, lam_q, lo, h, ng, k))
+    rhs = np.vdot(oracle_lib.p2p_st(q, p, mu, lo, h, ng, k, conj=True), lam_q)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_st_neighbors_independent(oracle_lib):
+    rng = np.random.default_rng(14)
+    ng = 9
+    t = (rng.random((400, 3)) * 0.6).astype(np.float32)          # targets in one corner
+    s = (rng.random((700, 3)) * 0.7 + 0.3).astype(np.float32)    # sources overlapping it partly
+    lo, h = (0, 0, 0), 1.0 / ng
+    bt, bs = oracle_lib.bin_points(t, lo, h, ng), oracle_lib.bin_points(s, lo, h, ng)
+    nptr, nidx = oracle_lib.neighbors_st(bt["box_keys"], bs["box_keys"], ng)
+    # independent construction from the cells of the points of each box
+    ct = _cells_numpy(t, lo, h, ng)[bt["perm"][bt["box_ptr"][:-1]]]
+    cs = _cells_numpy(s, lo, h, ng)[bs["perm"][bs["box_ptr"][:-1]]]
+    for b in range(bt["num_boxes"]):
+        want = np.nonzero(np.abs(cs - ct[b]).max(axis=1) <= 1)[0]
+        np.testing.assert_array_equal(nidx[nptr[b]:nptr[b + 1]], want)
+    assert nptr[-1] < 27 * bt["num_boxes"] and nptr[-1] > 0
+    # sampled targets equal the full evaluation
+    lam = W.strengths(700, 1, 14)
+    full = oracle_lib.p2p_st(t, s, lam, lo, h, ng, 4.0)
+    which = np.array([0, 17, 399, 200])
+    np.testing.assert_array_equal(oracle_lib.p2p_st_targets(t, s, lam, which, lo, h, ng, 4.0), full[which])
