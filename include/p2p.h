@@ -74,7 +74,8 @@ typedef enum {
     P2P_ERR_CUDA = 3,        /* a CUDA call failed; see p2p_last_error_string */
     P2P_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
     P2P_ERR_UNSUPPORTED = 5, /* valid request that this build/device does not support */
-    P2P_ERR_ALLOC = 6        /* host memory for the plan object could not be allocated */
+    P2P_ERR_ALLOC = 6,       /* host memory for the plan object could not be allocated */
+    P2P_ERR_STALE = 7        /* new coordinates move a point out of its leaf box: rebuild the plan */
 } p2p_status;
 
 typedef enum { P2P_HELMHOLTZ = 0, P2P_LAPLACE = 1 } p2p_kernel;
@@ -205,6 +206,31 @@ P2P_API p2p_status p2p_build_neighbors(const int64_t* box_keys, const int32_t* b
                                        int32_t ng, int32_t* nbr_ptr, int32_t* nbr_idx, int64_t* nnz,
                                        int64_t* sources, void* work, size_t work_bytes, p2p_stream_t stream);
 
+/*
+ * Neighbour lists between two point sets binned on the same grid (targets and
+ * sources kept as separate arrays, as the paper's tree object does, Sec. 3.1):
+ * for target box b, the non-empty SOURCE boxes whose cells lie within
+ * Chebyshev distance 1 of b's cell, in ascending source box id, and the
+ * position in that list of the source box of b's own cell (the only sources
+ * that can coincide with one of b's targets), or -1 if that cell holds no
+ * source.
+ *
+ *   tgt_keys, num_tgt_boxes  [dev] target box keys from p2p_bin_points on the targets (strictly ascending)
+ *   src_keys, src_box_ptr    [dev] source box keys and box pointers from p2p_bin_points on the sources
+ *   num_src_boxes, ng              as returned / passed to the two p2p_bin_points calls (same lo, h, ng)
+ *   nbr_ptr    [dev]  out, num_tgt_boxes + 1 int32
+ *   nbr_idx    [dev]  out, capacity 27 * num_tgt_boxes int32 (source box ids)
+ *   nbr_self   [dev]  out, num_tgt_boxes int32
+ *   nnz, sources [host] out, entries of the lists and the total of their source counts
+ *   work       [dev]  scratch of at least p2p_neighbors_workspace_size(num_tgt_boxes) bytes
+ *
+ * Synchronises to read back nnz and sources.
+ */
+P2P_API p2p_status p2p_build_neighbors_st(const int64_t* tgt_keys, int32_t num_tgt_boxes, const int64_t* src_keys,
+                                          const int32_t* src_box_ptr, int32_t num_src_boxes, int32_t ng,
+                                          int32_t* nbr_ptr, int32_t* nbr_idx, int32_t* nbr_self, int64_t* nnz,
+                                          int64_t* sources, void* work, size_t work_bytes, p2p_stream_t stream);
+
 /* ------------------------------------------------------------- plans --- */
 /*
  * A plan binds one point set and its box structure to a kernel, a wavenumber,
@@ -239,7 +265,56 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
                                    const int32_t* nbr_idx, int64_t nnz, int64_t sources, p2p_kernel kernel,
                                    float k, p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
                                    void* workspace, size_t workspace_bytes, p2p_stream_t stream);
+
+/*
+ * A plan between two point sets: out (n_tgt rows) = A lambda (n_src rows), the
+ * near-field operator from the sources to the targets, with the target boxes,
+ * source boxes and lists of p2p_bin_points (once per set, same lo, h and ng)
+ * and p2p_build_neighbors_st.  A target and a source at the same position
+ * (r = 0) are skipped.  Layouts INDEXED and REDUNDANT (SYMMETRIC returns
+ * P2P_ERR_UNSUPPORTED); every apply path, the batched launch and the host-buffer
+ * apply take such plans, with strengths of n_src rows and results of n_tgt rows.
+ * p2p_apply_adjoint and p2p_grad_points return P2P_ERR_UNSUPPORTED: the adjoint
+ * A^H g (n_src rows) is the plan with the two sets exchanged applied with
+ * adjoint = 1 in p2p_apply_path, since G(x, y) = G(y, x) (p2p_apply_path with
+ * adjoint = 1 on a two-set plan computes conj(A) lambda).  The tensor-core
+ * workspace term counts n_src / 16 + num_src_boxes groups.  Other arguments as
+ * for p2p_plan_create.
+ */
+P2P_API p2p_status p2p_plan_workspace_size_st(int64_t n_tgt, int32_t num_tgt_boxes, int64_t n_src,
+                                              int32_t num_src_boxes, int64_t nnz, int64_t sources, p2p_layout layout,
+                                              int32_t max_nrhs, const p2p_tuning* tuning, size_t* bytes);
+P2P_API p2p_status p2p_plan_create_st(p2p_plan** plan, const float* tgt_pts, int64_t n_tgt, const int32_t* tgt_perm,
+                                      const int32_t* tgt_box_ptr, int32_t num_tgt_boxes, const float* src_pts,
+                                      int64_t n_src, const int32_t* src_perm, const int32_t* src_box_ptr,
+                                      int32_t num_src_boxes, const int32_t* nbr_ptr, const int32_t* nbr_idx,
+                                      const int32_t* nbr_self, int64_t nnz, int64_t sources, p2p_kernel kernel,
+                                      float k, p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
+                                      void* workspace, size_t workspace_bytes, p2p_stream_t stream);
+
 P2P_API p2p_status p2p_plan_destroy(p2p_plan* plan);
+
+/*
+ * New coordinates for the points of a one-set plan whose box structure stays
+ * valid: every point must lie in the same leaf box (the same grid cell under
+ * lo, h, ng, the grid the structure was binned on) as the coordinates the plan
+ * holds now.  A shape-optimisation step that moves points by less than their
+ * distance to the box faces keeps the binning, the neighbour lists and the work
+ * items; only the box-sorted coordinates (and, for the redundant layout, the
+ * per-box copies of Sec. 3.3) are gathered again.
+ *
+ *   pts        [dev] n x 3 float, the new coordinates in original point order
+ *   lo, h, ng        the grid passed to p2p_bin_points for this plan
+ *   moved      [host] out (may be NULL): points whose cell would change
+ *
+ * Returns P2P_ERR_STALE, leaving the plan unchanged, if any point would change
+ * cell (rebuild the structure and the plan from the new coordinates);
+ * P2P_ERR_INVALID for a non-finite coordinate; P2P_ERR_UNSUPPORTED for a
+ * two-set plan.  On success the plan reads its coordinates from `pts` from now
+ * on (the previous array may be released).  Synchronises.
+ */
+P2P_API p2p_status p2p_plan_update_points(p2p_plan* plan, const float* pts, const double lo[3], double h, int32_t ng,
+                                          int64_t* moved, p2p_stream_t stream);
 
 /* Number of work items, ordered (target, source) pairs with r > 0 are not
  * counted here; see p2p_plan_pair_count. */

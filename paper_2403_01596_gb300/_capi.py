@@ -20,6 +20,7 @@ P2P_ERR_CUDA = 3
 P2P_ERR_TIMEOUT = 4
 P2P_ERR_UNSUPPORTED = 5
 P2P_ERR_ALLOC = 6
+P2P_ERR_STALE = 7
 
 P2P_HELMHOLTZ = 0
 P2P_LAPLACE = 1
@@ -77,7 +78,12 @@ def load(build_if_missing: bool = True):
             "p2p_bin_points_static": ([P, i64, P, dbl, i32, P, P, P, P, PI32, P], ctypes.c_int),
             "p2p_neighbors_workspace_size": ([i32, PSZ], ctypes.c_int),
             "p2p_build_neighbors": ([P, P, i32, i32, P, P, PI64, PI64, P, sz, P], ctypes.c_int),
+            "p2p_plan_update_points": ([P, P, P, dbl, i32, PI64, P], ctypes.c_int),
+            "p2p_build_neighbors_st": ([P, i32, P, P, i32, i32, P, P, P, PI64, PI64, P, sz, P], ctypes.c_int),
             "p2p_plan_workspace_size": ([i64, i32, i64, i64, ctypes.c_int, i32, P, PSZ], ctypes.c_int),
+            "p2p_plan_workspace_size_st": ([i64, i32, i64, i32, i64, i64, ctypes.c_int, i32, P, PSZ], ctypes.c_int),
+            "p2p_plan_create_st": ([ctypes.POINTER(P), P, i64, P, P, i32, P, i64, P, P, i32, P, P, P, i64, i64,
+                                    ctypes.c_int, flt, ctypes.c_int, i32, P, P, sz, P], ctypes.c_int),
             "p2p_plan_create": ([ctypes.POINTER(P), P, i64, P, P, i32, P, P, i64, i64, ctypes.c_int, flt,
                                  ctypes.c_int, i32, P, P, sz, P], ctypes.c_int),
             "p2p_plan_destroy": ([P], ctypes.c_int),
@@ -174,6 +180,17 @@ def p2p_build_neighbors(box_keys, box_ptr, num_boxes, ng, nbr_ptr, nbr_idx, work
     return nnz.value, src.value
 
 
+def p2p_build_neighbors_st(tgt_keys, num_tgt_boxes, src_keys, src_box_ptr, num_src_boxes, ng, nbr_ptr, nbr_idx,
+                           nbr_self, work, stream=None):
+    nnz, src = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = load().p2p_build_neighbors_st(_ptr(tgt_keys), int(num_tgt_boxes), _ptr(src_keys), _ptr(src_box_ptr),
+                                       int(num_src_boxes), int(ng), _ptr(nbr_ptr), _ptr(nbr_idx), _ptr(nbr_self),
+                                       ctypes.byref(nnz), ctypes.byref(src), _ptr(work), work.numel(),
+                                       _stream(stream))
+    check(st, "p2p_build_neighbors_st")
+    return nnz.value, src.value
+
+
 def _tuning(t):
     if t is None:
         return None
@@ -199,6 +216,29 @@ def p2p_plan_create(pts, perm, box_ptr, num_boxes, nbr_ptr, nbr_idx, nnz, source
     return plan
 
 
+def p2p_plan_workspace_size_st(n_tgt, num_tgt_boxes, n_src, num_src_boxes, nnz, sources, layout, max_nrhs,
+                               tuning=None) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().p2p_plan_workspace_size_st(n_tgt, num_tgt_boxes, n_src, num_src_boxes, nnz, sources, layout,
+                                            max_nrhs, _tuning(tuning), ctypes.byref(out)),
+          "p2p_plan_workspace_size_st")
+    return out.value
+
+
+def p2p_plan_create_st(tgt_pts, tgt_perm, tgt_box_ptr, num_tgt_boxes, src_pts, src_perm, src_box_ptr, num_src_boxes,
+                       nbr_ptr, nbr_idx, nbr_self, nnz, sources, kernel, k, layout, max_nrhs, tuning, workspace,
+                       stream=None) -> ctypes.c_void_p:
+    plan = ctypes.c_void_p(0)
+    st = load().p2p_plan_create_st(ctypes.byref(plan), _ptr(tgt_pts), tgt_pts.shape[0], _ptr(tgt_perm),
+                                   _ptr(tgt_box_ptr), int(num_tgt_boxes), _ptr(src_pts), src_pts.shape[0],
+                                   _ptr(src_perm), _ptr(src_box_ptr), int(num_src_boxes), _ptr(nbr_ptr),
+                                   _ptr(nbr_idx), _ptr(nbr_self), int(nnz), int(sources), int(kernel), float(k),
+                                   int(layout), int(max_nrhs), _tuning(tuning), _ptr(workspace), workspace.numel(),
+                                   _stream(stream))
+    check(st, "p2p_plan_create_st")
+    return plan
+
+
 def p2p_plan_destroy(plan):
     if plan:
         load().p2p_plan_destroy(plan)
@@ -213,6 +253,18 @@ def p2p_plan_info(plan) -> dict:
     return {"n": n.value, "num_boxes": nb.value, "sources": src.value, "work_items": items.value,
             "layout": layout.value, "tuning": {"chunk": t.chunk, "warps_per_cta": t.warps_per_cta,
                                                "target_group": t.target_group}}
+
+
+def p2p_plan_update_points(plan, pts, lo, h, ng, stream=None):
+    """New coordinates for a plan; returns (status, moved): P2P_OK, or P2P_ERR_STALE when `moved` points would
+    change leaf box (the plan is then unchanged).  Other failures raise."""
+    lo_arr = (ctypes.c_double * 3)(*[float(v) for v in lo])
+    moved = ctypes.c_int64(0)
+    st = load().p2p_plan_update_points(plan, _ptr(pts), lo_arr, float(h), int(ng), ctypes.byref(moved),
+                                       _stream(stream))
+    if st not in (P2P_OK, P2P_ERR_STALE):
+        check(st, "p2p_plan_update_points")
+    return st, moved.value
 
 
 def p2p_plan_pair_count(plan, stream=None) -> int:

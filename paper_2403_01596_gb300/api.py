@@ -34,8 +34,8 @@ def _bytes(n: int, device) -> torch.Tensor:
     return torch.empty(max(int(n), 1), dtype=torch.uint8, device=device)
 
 
-class BoxStructure:
-    """Leaf binning + neighbour lists of one point set (device tensors)."""
+class Binning:
+    """Leaf binning of one point set (device tensors): perm, point_box, box_keys, box_ptr."""
 
     def __init__(self, points: torch.Tensor, lo, h: float, ng: int):
         if not points.is_cuda:
@@ -58,13 +58,23 @@ class BoxStructure:
         B = self.num_boxes
         self.box_keys = keys[:B].clone() if B else keys[:0]
         self.box_ptr = ptr[:B + 1].clone()
+        self.n = n
+
+
+class BoxStructure(Binning):
+    """Leaf binning + neighbour lists of one point set (device tensors)."""
+
+    def __init__(self, points: torch.Tensor, lo, h: float, ng: int):
+        super().__init__(points, lo, h, ng)
+        dev = self.points.device
+        s = _stream()
+        B = self.num_boxes
         self.nbr_ptr = torch.empty(B + 1, dtype=torch.int32, device=dev)
         self.nbr_idx = torch.empty(max(27 * B, 1), dtype=torch.int32, device=dev)
         work = _bytes(C.p2p_neighbors_workspace_size(B), dev)
         self.nnz, self.sources = C.p2p_build_neighbors(self.box_keys, self.box_ptr, B, self.ng, self.nbr_ptr,
                                                        self.nbr_idx, work, s)
         del work
-        self.n = n
 
 
 class Plan:
@@ -73,11 +83,16 @@ class Plan:
     def __init__(self, points: torch.Tensor, lo, h: float, ng: int, k: float = 0.0, kernel: str = "helmholtz",
                  layout: str = "indexed", max_nrhs: int = 1, tuning: dict | None = None,
                  structure: BoxStructure | None = None):
-        self.structure = structure if structure is not None else BoxStructure(points, lo, h, ng)
-        st = self.structure
         self.kernel, self.layout, self.k = kernel, layout, float(k)
         self.max_nrhs = int(max_nrhs)
         self.tuning = tuning
+        self._build(structure if structure is not None else BoxStructure(points, lo, h, ng))
+        self.rebuilds = 0
+
+    def _build(self, structure: "BoxStructure"):
+        self.structure = structure
+        st = self.structure
+        kernel, layout, tuning = self.kernel, self.layout, self.tuning
         dev = st.points.device
         ws = C.p2p_plan_workspace_size(st.n, st.num_boxes, st.nnz, st.sources, LAYOUTS[layout], self.max_nrhs,
                                        tuning)
@@ -87,6 +102,31 @@ class Plan:
                                        self.workspace, _stream())
         self.info = C.p2p_plan_info(self._plan)
         self._pairs = None
+        self._seen = (st.points.data_ptr(), st.points._version)
+
+    # ------------------------------------------------------ moving points --
+    def update_points(self, points: torch.Tensor) -> bool:
+        """Takes new coordinates for the plan's points (original order).  Returns True when every point stays in
+        its leaf box (only the coordinates are gathered again), else rebuilds the box structure and the plan from
+        the new coordinates on the same grid and returns False."""
+        pts = points.detach().contiguous()
+        if pts.shape != self.structure.points.shape or pts.dtype != torch.float32 or not pts.is_cuda:
+            raise ValueError("new coordinates must be a float32 CUDA tensor of the plan's shape")
+        st = self.structure
+        status, _ = C.p2p_plan_update_points(self._plan, pts, st.lo, st.h, st.ng, _stream())
+        if status == C.P2P_OK:
+            st.points = pts      # the plan reads this array from now on
+            self._seen = (pts.data_ptr(), pts._version)
+            return True
+        self.close()
+        self._build(BoxStructure(pts, st.lo, st.h, st.ng))
+        self.rebuilds += 1
+        return False
+
+    def follow(self, points: torch.Tensor):
+        """update_points(points) if `points` is not the array (and version) the plan last took."""
+        if (points.data_ptr(), points._version) != self._seen:
+            self.update_points(points)
 
     # ----------------------------------------------------------------- info --
     @property
@@ -94,8 +134,17 @@ class Plan:
         return self.structure.n
 
     @property
+    def n_src(self) -> int:
+        """Rows of the strengths (the sources; the points themselves for a one-set plan)."""
+        return self.structure.n
+
+    @property
     def num_boxes(self) -> int:
         return self.structure.num_boxes
+
+    @property
+    def device(self):
+        return self.workspace.device
 
     def pair_count(self) -> int:
         if self._pairs is None:
@@ -106,12 +155,13 @@ class Plan:
         return C.p2p_last_async_status(self._plan, _stream())
 
     # ---------------------------------------------------------------- apply --
-    def _check_lam(self, lam: torch.Tensor):
+    def _check_lam(self, lam: torch.Tensor, rows: int | None = None):
+        rows = self.n_src if rows is None else rows
         if not lam.is_cuda or lam.dtype != torch.complex64:
             raise ValueError("strengths must be a complex64 CUDA tensor")
-        if lam.shape[0] != self.n:
-            raise ValueError(f"expected {self.n} rows, got {lam.shape[0]}")
-        lam2 = lam.reshape(self.n, 1) if lam.dim() == 1 else lam
+        if lam.shape[0] != rows:
+            raise ValueError(f"expected {rows} rows, got {lam.shape[0]}")
+        lam2 = lam.reshape(rows, 1) if lam.dim() == 1 else lam
         if lam2.dim() != 2:
             raise ValueError("strengths must have shape (n,) or (n, nrhs)")
         if lam2.stride(1) != 1:
@@ -148,6 +198,87 @@ class Plan:
             pass
 
 
+class TwoSetStructure:
+    """Binnings of a target set and a source set on one grid, and the target-box -> source-box neighbour lists
+    (with the position of each target box's own-cell source box, nbr_self)."""
+
+    def __init__(self, targets: torch.Tensor, sources: torch.Tensor, lo, h: float, ng: int,
+                 tgt: Binning | None = None, src: Binning | None = None):
+        self.tgt = tgt if tgt is not None else Binning(targets, lo, h, ng)
+        self.src = src if src is not None else Binning(sources, lo, h, ng)
+        t, sb = self.tgt, self.src
+        dev = t.points.device
+        B = t.num_boxes
+        self.nbr_ptr = torch.empty(B + 1, dtype=torch.int32, device=dev)
+        self.nbr_idx = torch.empty(max(27 * B, 1), dtype=torch.int32, device=dev)
+        self.nbr_self = torch.empty(max(B, 1), dtype=torch.int32, device=dev)
+        work = _bytes(C.p2p_neighbors_workspace_size(B), dev)
+        self.nnz, self.sources = C.p2p_build_neighbors_st(t.box_keys, B, sb.box_keys, sb.box_ptr, sb.num_boxes,
+                                                          t.ng, self.nbr_ptr, self.nbr_idx, self.nbr_self, work,
+                                                          _stream())
+        del work
+
+    def exchanged(self) -> "TwoSetStructure":
+        """The same two binnings with the roles of targets and sources exchanged."""
+        return TwoSetStructure(self.src.points, self.tgt.points, self.tgt.lo, self.tgt.h, self.tgt.ng,
+                               tgt=self.src, src=self.tgt)
+
+
+class TwoSetPlan(Plan):
+    """out (n_tgt rows) = A lam (n_src rows): the near field from a source point set to a separate target point
+    set binned on the same grid.  plan.apply(lam), plan.adjoint_plan().apply(g, adjoint=True) = A^H g."""
+
+    def __init__(self, targets: torch.Tensor, sources: torch.Tensor, lo, h: float, ng: int, k: float = 0.0,
+                 kernel: str = "helmholtz", layout: str = "indexed", max_nrhs: int = 1, tuning: dict | None = None,
+                 structure: TwoSetStructure | None = None):
+        self.structure = structure if structure is not None else TwoSetStructure(targets, sources, lo, h, ng)
+        st = self.structure
+        t, sb = st.tgt, st.src
+        self.kernel, self.layout, self.k = kernel, layout, float(k)
+        self.max_nrhs = int(max_nrhs)
+        self.tuning = tuning
+        ws = C.p2p_plan_workspace_size_st(t.n, t.num_boxes, sb.n, sb.num_boxes, st.nnz, st.sources,
+                                          LAYOUTS[layout], self.max_nrhs, tuning)
+        self.workspace = _bytes(ws, t.points.device)
+        self._plan = C.p2p_plan_create_st(t.points, t.perm, t.box_ptr, t.num_boxes, sb.points, sb.perm, sb.box_ptr,
+                                          sb.num_boxes, st.nbr_ptr, st.nbr_idx, st.nbr_self, st.nnz, st.sources,
+                                          KERNELS[kernel], self.k, LAYOUTS[layout], self.max_nrhs, tuning,
+                                          self.workspace, _stream())
+        self.info = C.p2p_plan_info(self._plan)
+        self._pairs = None
+
+    @property
+    def n(self) -> int:
+        return self.structure.tgt.n
+
+    @property
+    def n_src(self) -> int:
+        return self.structure.src.n
+
+    @property
+    def num_boxes(self) -> int:
+        return self.structure.tgt.num_boxes
+
+    def apply(self, lam: torch.Tensor, out: torch.Tensor | None = None, adjoint: bool = False,
+              path: str = "auto") -> torch.Tensor:
+        """A lam (adjoint=True: conj(A) lam, which is the adjoint of the plan with the sets exchanged)."""
+        lam2 = self._check_lam(lam).contiguous()
+        nrhs = lam2.shape[1]
+        if out is None:
+            out = torch.empty((self.n, nrhs), dtype=torch.complex64, device=lam.device)
+        C.p2p_apply_path(self._plan, lam2, out, nrhs, nrhs, int(adjoint), PATHS[path], _stream())
+        return out.reshape(self.n) if lam.dim() == 1 else out
+
+    def adjoint_plan(self) -> "TwoSetPlan":
+        """The plan with targets and sources exchanged; its apply(g, adjoint=True) is A^H g."""
+        st = self.structure.exchanged()
+        return TwoSetPlan(st.tgt.points, st.src.points, st.tgt.lo, st.tgt.h, st.tgt.ng, self.k, self.kernel,
+                          self.layout, self.max_nrhs, self.tuning, structure=st)
+
+    def grad_points(self, lam, g):
+        raise NotImplementedError("coordinate gradients are provided for one-set plans")
+
+
 class Batch:
     """Several plans applied in one persistent launch (optionally replayed from a CUDA graph)."""
 
@@ -155,7 +286,7 @@ class Batch:
         self.plans = list(plans)
         self.nrhs = int(nrhs)
         handles = [p._plan for p in self.plans]
-        dev = self.plans[0].structure.points.device
+        dev = self.plans[0].device
         self.workspace = _bytes(C.p2p_batch_workspace_size(handles, self.nrhs), dev)
         self._b = C.p2p_batch_create(handles, self.nrhs, warps_per_cta, self.workspace, _stream())
         self.info = C.p2p_batch_info(self._b)
@@ -169,8 +300,9 @@ class Batch:
             if l.shape[1] != self.nrhs:
                 raise ValueError(f"expected {self.nrhs} right-hand sides")
         if outs is None:
-            outs = [torch.empty_like(l) for l in lam2]
-        outs2 = [o.reshape(l.shape) for o, l in zip(outs, lam2)]
+            outs = [torch.empty((p.n, self.nrhs), dtype=torch.complex64, device=l.device)
+                    for p, l in zip(self.plans, lam2)]
+        outs2 = [o.reshape(p.n, self.nrhs) for o, p in zip(outs, self.plans)]
         return lam2, outs2
 
     def apply(self, lams, outs=None):
@@ -223,14 +355,15 @@ class HostPipe:
         for p, l in zip(plans, lams_host):
             if l.device.type != "cpu" or l.dtype != torch.complex64 or not l.is_contiguous():
                 raise ValueError("host strengths must be contiguous complex64 CPU tensors")
-            if l.numel() != p.n * self.nrhs:
-                raise ValueError(f"expected {p.n} x {self.nrhs} strengths")
+            if l.numel() != p.n_src * self.nrhs:
+                raise ValueError(f"expected {p.n_src} x {self.nrhs} strengths")
             lam2.append(l)
         if outs_host is None:
-            outs_host = [torch.empty_like(l, pin_memory=True) for l in lam2]
-        for o, l in zip(outs_host, lam2):
-            if o.device.type != "cpu" or o.dtype != torch.complex64 or not o.is_contiguous() or o.numel() != l.numel():
-                raise ValueError("host results must be contiguous complex64 CPU tensors shaped like the strengths")
+            outs_host = [torch.empty(p.n * self.nrhs, dtype=torch.complex64, pin_memory=True) for p in plans]
+        for o, p in zip(outs_host, plans):
+            if (o.device.type != "cpu" or o.dtype != torch.complex64 or not o.is_contiguous()
+                    or o.numel() != p.n * self.nrhs):
+                raise ValueError("host results must be contiguous complex64 CPU tensors of n x nrhs elements")
         C.p2p_apply_host(self._p, [p._plan for p in plans], lam2, outs_host, _stream())
         return outs_host
 
@@ -263,12 +396,17 @@ def choose_grid_ct(points: torch.Tensor, lo, extent: float, ct: int, ng_start: i
 class P2PFunction(torch.autograd.Function):
     """out = A(x) lam with gradients for lam (A^H g) and for x (radial-derivative kernel).
 
-    The box structure of the plan is held fixed: a coordinate gradient is the
-    derivative for a perturbation that moves no point across a box face.
+    The plan follows the coordinates it is given: when `points` is not the
+    array (or version of it) the plan last took, the plan takes the new
+    coordinates (p2p_plan_update_points) or, when a point has left its leaf
+    box, is rebuilt from them on the same grid.  A coordinate gradient is the
+    derivative with box membership held fixed (a perturbation that moves no
+    point across a box face).
     """
 
     @staticmethod
     def forward(ctx, lam, points, plan: Plan):
+        plan.follow(points)
         ctx.plan = plan
         ctx.save_for_backward(lam)
         return plan.apply(lam)

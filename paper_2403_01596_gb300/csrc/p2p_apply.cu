@@ -44,7 +44,7 @@ __device__ __forceinline__ void grad_targets(const PairArgs& a, const float4* __
     for (int u = 0; u < TT; ++u) {
         const int t = g + u * G;
         const bool ok = t < nt;
-        tx[u] = ok ? a.xs[tbase + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tx[u] = ok ? a.xt[tbase + t] : make_float4(0.f, 0.f, 0.f, 0.f);
         tl[u] = ok ? a.lam[(int64_t)(tbase + t) * a.nrhs + rhs] : make_float2(0.f, 0.f);
         tgv[u] = ok ? a.gsrc[(int64_t)(tbase + t) * a.nrhs + rhs] : make_float2(0.f, 0.f);
         acc[u][0] = acc[u][1] = acc[u][2] = 0.f;
@@ -319,9 +319,10 @@ p2p_status launch_pair(const p2p_plan* p, const PairArgs& a, cudaStream_t s) {
     return P2P_OK;
 }
 
+// lam: strengths (one row per source, may be NULL when there are none); out: results (one row per target).
 p2p_status check_apply_args(const p2p_plan* plan, const void* lam, const void* out, int32_t nrhs, int64_t ld) {
     if (!plan || nrhs < 1 || nrhs > plan->max_nrhs || ld < nrhs) return P2P_ERR_INVALID;
-    if (plan->n > 0 && (!lam || !out)) return P2P_ERR_INVALID;
+    if ((plan->n_src > 0 && !lam) || (plan->n > 0 && !out)) return P2P_ERR_INVALID;
     if (((uintptr_t)lam & 7) || ((uintptr_t)out & 7)) return P2P_ERR_INVALID;
     return P2P_OK;
 }
@@ -351,38 +352,45 @@ static p2p_path resolve_path(const p2p_plan* plan, int32_t nrhs, p2p_path path) 
 
 P2P_API p2p_status p2p_apply_stage(const p2p_plan* plan, const void* lambda, int32_t nrhs, int64_t ld, p2p_path path,
                                    p2p_stream_t stream) {
-    p2p_status st = check_apply_args(plan, lambda, lambda, nrhs, ld);
+    if (!plan) return P2P_ERR_INVALID;
+    p2p_status st = check_apply_args(plan, lambda, plan->n > 0 ? plan : nullptr, nrhs, ld);
     if (st != P2P_OK) return st;
     if (path < P2P_PATH_AUTO || path > P2P_PATH_TC_BF16X3) return P2P_ERR_INVALID;
-    if (plan->n == 0) return P2P_OK;
+    if (plan->n == 0 || plan->n_src == 0) return P2P_OK;
     path = resolve_path(plan, nrhs, path);
     if (path == P2P_PATH_TC_BF16X3 && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if (path == P2P_PATH_TC_BF16X3) return p2p_tc_stage(plan, (const float2*)lambda, nrhs, ld, s);
     const bool red = plan->layout == P2P_LAYOUT_REDUNDANT;
-    const int32_t* rows = red ? plan->pk_src : plan->perm;
-    const int64_t nrows = red ? plan->packed : plan->n;
+    const int32_t* rows = red ? plan->pk_src : plan->src_perm;  // strengths live on the sources
+    const int64_t nrows = red ? plan->packed : plan->n_src;
     P2P_TRY_CUDA(stage_rows((const float2*)lambda, ld, rows, nrows, nrhs, plan->lam_buf, s), "p2p_apply_stage");
     return P2P_OK;
 }
 
 P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrhs, int64_t ld, int32_t adjoint,
                                     p2p_path path, p2p_stream_t stream) {
-    p2p_status st = check_apply_args(plan, out, out, nrhs, ld);
+    if (!plan) return P2P_ERR_INVALID;
+    p2p_status st = check_apply_args(plan, plan->n_src > 0 ? plan : nullptr, out, nrhs, ld);
     if (st != P2P_OK) return st;
     if (path < P2P_PATH_AUTO || path > P2P_PATH_TC_BF16X3) return P2P_ERR_INVALID;
     if (plan->n == 0) return P2P_OK;
     path = resolve_path(plan, nrhs, path);
     if (path == P2P_PATH_TC_BF16X3 && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
+    // a two-set plan may have target boxes without any source nearby: no item or unit writes their rows
+    if (plan->two_sets)
+        P2P_TRY_CUDA(cudaMemset2DAsync(out, (size_t)ld * 8, 0, (size_t)nrhs * 8, (size_t)plan->n, s), "p2p_apply/zero");
+    if (plan->n_src == 0) return P2P_OK;
     if (path == P2P_PATH_TC_BF16X3) return p2p_apply_tc(plan, (float2*)out, nrhs, ld, adjoint, s);
     PairArgs a = base_args(plan);
     a.out = (float2*)out;
     a.ld = ld;
     a.nrhs = nrhs;
     if (adjoint) a.k = -a.k;
-    if (a.atomic_out)
+    if (a.atomic_out && !plan->two_sets)
         P2P_TRY_CUDA(cudaMemset2DAsync(out, (size_t)ld * 8, 0, (size_t)nrhs * 8, (size_t)plan->n, s), "p2p_apply/zero");
+    if (plan->n_items == 0) return P2P_OK;
     const int R = path == P2P_PATH_FP32_PER_RHS ? 1 : (nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1));
     return R == 1 ? launch_pair<1>(plan, a, s) : (R == 2 ? launch_pair<2>(plan, a, s) : launch_pair<4>(plan, a, s));
 }
@@ -391,7 +399,7 @@ P2P_API p2p_status p2p_apply_path(const p2p_plan* plan, const void* lambda, void
                                   int32_t adjoint, p2p_path path, p2p_stream_t stream) {
     p2p_status st = check_apply_args(plan, lambda, out, nrhs, ld);
     if (st != P2P_OK) return st;
-    if (lambda == out && plan->n > 0) return P2P_ERR_INVALID;
+    if (lambda == out && plan->n > 0 && plan->n_src > 0) return P2P_ERR_INVALID;
     st = p2p_apply_stage(plan, lambda, nrhs, ld, path, stream);
     if (st != P2P_OK) return st;
     return p2p_apply_staged(plan, out, nrhs, ld, adjoint, path, stream);
@@ -404,6 +412,8 @@ P2P_API p2p_status p2p_apply(const p2p_plan* plan, const void* lambda, void* out
 
 P2P_API p2p_status p2p_apply_adjoint(const p2p_plan* plan, const void* g, void* out, int32_t nrhs, int64_t ld,
                                      p2p_stream_t stream) {
+    // a two-set operator's adjoint maps target space to source space: a plan with the roles exchanged
+    if (plan && plan->two_sets) return P2P_ERR_UNSUPPORTED;
     return p2p_apply_path(plan, g, out, nrhs, ld, 1, P2P_PATH_AUTO, stream);
 }
 
@@ -414,6 +424,7 @@ P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, con
     if (plan->n == 0) return P2P_OK;
     if (!grad || ((uintptr_t)grad & 3)) return P2P_ERR_INVALID;
     if (plan->layout == P2P_LAYOUT_SYMMETRIC) return P2P_ERR_UNSUPPORTED;  // needs the full source lists
+    if (plan->two_sets) return P2P_ERR_UNSUPPORTED;                         // one point set only
     cudaStream_t s = (cudaStream_t)stream;
     P2P_TRY_CUDA(stage_rows((const float2*)lambda, ld, plan->perm, plan->n, nrhs, plan->lam_buf, s),
                  "p2p_grad_points/stage");

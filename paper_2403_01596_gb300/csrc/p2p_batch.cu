@@ -265,13 +265,15 @@ P2P_API p2p_status p2p_batch_create(p2p_batch** batch, const p2p_plan* const* pl
         host[g].a = base_args(p);
         host[g].a.nrhs = nrhs;
         host[g].n = p->n;
-        host[g].nrows = host[g].a.red ? p->packed : p->n;
-        host[g].rows = host[g].a.red ? p->pk_src : p->perm;
+        host[g].nrows = host[g].a.red ? p->packed : p->n_src;   // staged strengths live on the sources
+        host[g].rows = host[g].a.red ? p->pk_src : p->src_perm;
         max_chunk = std::max(max_chunk, p->tune.chunk);
         if (host[g].a.sym) b->sym_any = 1;
         off.off[g + 1] = off.off[g] + p->n_items;
         b->io.row_off[g + 1] = b->io.row_off[g] + host[g].nrows * nrhs;
-        b->io.out_off[g + 1] = b->io.out_off[g] + (host[g].a.atomic_out ? p->n * nrhs : 0);
+        // outputs accumulated with atomics, and two-set plans (targets without nearby sources get no item),
+        // are zeroed by the staging kernel
+        b->io.out_off[g + 1] = b->io.out_off[g] + ((host[g].a.atomic_out || p->two_sets) ? p->n * nrhs : 0);
     }
     b->chunk_max = max_chunk;
     b->warp_bytes = warp_smem_bytes(max_chunk, b->R, b->sym_any != 0);
@@ -302,8 +304,10 @@ P2P_API p2p_status p2p_batch_create(p2p_batch** batch, const p2p_plan* const* pl
     b->grid = ctas_per_sm * sms;
     FAIL(cudaMemcpyAsync(L.geoms, host, sizeof(BatchGeom) * count, cudaMemcpyHostToDevice, s), "p2p_batch_create");
     const unsigned blocks = (unsigned)((total + 255) / 256);
-    k_batch_order<<<blocks, 256, 0, s>>>(L.geoms, off, L.order);
-    FAIL(cudaGetLastError(), "p2p_batch_create/order");
+    if (blocks) {
+        k_batch_order<<<blocks, 256, 0, s>>>(L.geoms, off, L.order);
+        FAIL(cudaGetLastError(), "p2p_batch_create/order");
+    }
     FAIL(cudaStreamSynchronize(s), "p2p_batch_create");
 #undef FAIL
     *batch = b;

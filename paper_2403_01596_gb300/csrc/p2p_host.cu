@@ -71,7 +71,7 @@ P2P_API p2p_status p2p_apply_host(p2p_host_pipe* pipe, const p2p_plan* const* pl
     const int32_t nrhs = pipe->nrhs;
     for (int g = 0; g < count; ++g) {
         const p2p_plan* pl = plans[g];
-        if (!pl || pl->n > pipe->max_n || pl->max_nrhs < nrhs) return P2P_ERR_INVALID;
+        if (!pl || pl->n > pipe->max_n || pl->n_src > pipe->max_n || pl->max_nrhs < nrhs) return P2P_ERR_INVALID;
         if (pl->n > 0 && (!lambdas[g] || !outs[g])) return P2P_ERR_INVALID;
     }
     cudaStream_t s = (cudaStream_t)stream, c = pipe->copy;
@@ -79,7 +79,7 @@ P2P_API p2p_status p2p_apply_host(p2p_host_pipe* pipe, const p2p_plan* const* pl
     // up(g + 2) follows down(g), which waited for plan g's kernels: slot g % 2 is free when it is refilled.
     auto upload = [&](int g) -> cudaError_t {
         const int sl = g & 1;
-        const size_t bytes = (size_t)plans[g]->n * nrhs * 8;
+        const size_t bytes = (size_t)plans[g]->n_src * nrhs * 8;  // strengths: one row per source
         cudaError_t e = bytes ? cudaMemcpyAsync(pipe->lam[sl], lambdas[g], bytes, cudaMemcpyHostToDevice, c)
                               : cudaSuccess;
         return e == cudaSuccess ? cudaEventRecord(pipe->in_ready[sl], c) : e;

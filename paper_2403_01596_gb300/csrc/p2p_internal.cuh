@@ -57,9 +57,14 @@ __host__ __device__ inline int32_t p2p_lane_map(int nt, int ns) {
 }
 
 struct p2p_plan {
-    // sizes and parameters
+    // sizes and parameters.  n, nb, pts, perm, box_ptr and xs describe the TARGET points and their boxes (work
+    // items, outputs); the src_* fields describe the SOURCE points.  A one-set plan (sources = targets) has
+    // src_* equal to the target fields; a two-set plan (p2p_plan_create_st) has its own.
     int64_t n;
     int32_t nb;
+    int32_t two_sets;       // 1: separate target and source point sets
+    int64_t n_src;          // source points
+    int32_t nbs;            // source boxes
     int64_t nnz;
     int64_t sources;        // sum over boxes of S_b
     int64_t packed;         // padded packed size (redundant layout), 0 otherwise
@@ -74,8 +79,14 @@ struct p2p_plan {
     const int32_t* box_ptr;
     const int32_t* nbr_ptr;
     const int32_t* nbr_idx;
+    const float* src_pts;
+    const int32_t* src_perm;
+    const int32_t* src_box_ptr;
+    const int32_t* nbr_self;  // two-set plans: position in each target box's list of the source box of the same
+                              // cell, -1 if none (NULL for one-set plans: the box itself)
     // carved from the caller's workspace
-    float4* xs;             // [n] box-sorted coordinates (w = 0)
+    float4* xs;             // [n] box-sorted target coordinates (w = 0)
+    float4* xs_src;         // [n_src] box-sorted source coordinates (= xs for one-set plans)
     int32_t* box_src;       // [nb] S_b, sources in the neighbourhood of box b
     ItemRec* items;         // [n_items] work items, heaviest first
     int64_t n_items;

@@ -54,7 +54,8 @@ constexpr uint32_t kBulkWaitLimit = 1u << 24;
 struct PairArgs {
     const ItemRec* items;
     int64_t n_items;
-    const float4* xs;       // box-sorted coordinates (targets; indexed sources)
+    const float4* xs;       // box-sorted source coordinates (indexed layout)
+    const float4* xt;       // box-sorted target coordinates (= xs when sources are the targets)
     const float4* pk_xyz;   // redundant layout: per-box source tiles
     const int32_t* nb_src;  // per-box source lists (box-sorted indices)
     const float2* lam;      // staged strengths, row stride nrhs: sorted (indexed) or packed (redundant)
@@ -345,7 +346,7 @@ __device__ __forceinline__ void sweep_targets(const PairArgs& a, const float4* _
     for (int u = 0; u < TT; ++u) {
         const int t = g + u * G;
         // targets staged with the chunk (own box first) come from shared memory
-        tx[u] = t < nt ? (tsm >= 0 && tsm + t < m_end ? sx[tsm + t] : a.xs[tbase + t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        tx[u] = t < nt ? (tsm >= 0 && tsm + t < m_end ? sx[tsm + t] : a.xt[tbase + t]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[u][r] = make_float2(0.f, 0.f);
     }
@@ -435,7 +436,7 @@ __device__ __forceinline__ void sweep_targets_sym(const PairArgs& a, const float
         const int t = g + u * G;
         const bool ok = t < nt && q < Q;
         const bool staged = tsm >= 0 && tsm + t < m_end;  // target staged with the chunk
-        tx[u] = ok ? (staged ? sx[tsm + t] : a.xs[tbase + t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        tx[u] = ok ? (staged ? sx[tsm + t] : a.xt[tbase + t]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             tl[u][r] = (ok && rb + r < a.nrhs)
@@ -714,7 +715,8 @@ inline PairArgs base_args(const p2p_plan* p) {
     PairArgs a;
     a.items = p->items;
     a.n_items = p->n_items;
-    a.xs = p->xs;
+    a.xs = p->xs_src;
+    a.xt = p->xs;
     a.pk_xyz = p->pk_xyz;
     a.nb_src = p->nb_src;
     a.lam = p->lam_buf;

@@ -105,12 +105,13 @@ __device__ __forceinline__ int32_t warp_sort_asc(int32_t v, int lane) {
     return v;
 }
 
-// One warp per box; lane l < 27 probes the offset (l%3-1, (l/3)%3-1, l/9-1).
-template <bool FILL>
-__global__ void k_neighbors(const int64_t* __restrict__ box_keys, const int32_t* __restrict__ box_ptr, int32_t nb,
-                            int ng, int32_t* __restrict__ cnt, int32_t* __restrict__ src_cnt,
-                            const int32_t* __restrict__ nbr_ptr, int32_t* __restrict__ nbr_idx,
-                            int32_t* __restrict__ bad) {
+// One warp per target box; lane l < 27 probes the offset (l%3-1, (l/3)%3-1, l/9-1)
+// among the source boxes' keys (the same keys for a one-set structure, TWO = false).
+template <bool FILL, bool TWO>
+__global__ void k_neighbors(const int64_t* __restrict__ box_keys, int32_t nb, const int64_t* __restrict__ src_keys,
+                            int32_t nbs, const int32_t* __restrict__ src_box_ptr, int ng, int32_t* __restrict__ cnt,
+                            int32_t* __restrict__ src_cnt, const int32_t* __restrict__ nbr_ptr,
+                            int32_t* __restrict__ nbr_idx, int32_t* __restrict__ nbr_self, int32_t* __restrict__ bad) {
     const int lane = threadIdx.x & 31;
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
@@ -120,23 +121,34 @@ __global__ void k_neighbors(const int64_t* __restrict__ box_keys, const int32_t*
     if (lane < 27) {
         int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
         if (x >= 0 && y >= 0 && z >= 0 && x < ng && y < ng && z < ng)
-            id = find_key(box_keys, nb, (int64_t)p2p_morton(x, y, z));
+            id = find_key(src_keys, nbs, (int64_t)p2p_morton(x, y, z));
     }
     const unsigned found = __ballot_sync(P2P_FULL_MASK, id >= 0);
     if (!FILL) {
-        int s = id >= 0 ? box_ptr[id + 1] - box_ptr[id] : 0;
+        int s = id >= 0 ? src_box_ptr[id + 1] - src_box_ptr[id] : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(P2P_FULL_MASK, s, o);
         if (lane == 0) {
             cnt[b] = __popc(found);
             src_cnt[b] = s;
             if (b > 0 && box_keys[b - 1] >= box_keys[b]) *bad = 1;  // keys must strictly ascend
-            if (!((found >> 13) & 1u)) *bad = 1;                     // a box must find itself
+            if (!TWO && !((found >> 13) & 1u)) *bad = 1;             // a box must find itself
         }
     } else {
         int32_t v = warp_sort_asc(id >= 0 ? id : INT32_MAX, lane);
         if (lane < __popc(found)) nbr_idx[nbr_ptr[b] + lane] = v;
+        if (TWO) {
+            // position of the source box of the target box's own cell (probe 13) in the sorted list
+            const int32_t self = __shfl_sync(P2P_FULL_MASK, id, 13);
+            const unsigned at = __ballot_sync(P2P_FULL_MASK, self >= 0 && v == self);
+            if (lane == 0) nbr_self[b] = at ? __ffs(at) - 1 : -1;
+        }
     }
+}
+
+__global__ void k_keys_ascending(const int64_t* __restrict__ keys, int32_t n, int32_t* __restrict__ bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > 0 && i < n && keys[i - 1] >= keys[i]) *bad = 1;
 }
 
 __global__ void k_sum_i32(const int32_t* __restrict__ v, int64_t n, unsigned long long* __restrict__ out) {
@@ -157,37 +169,50 @@ __global__ void k_gather_xyz(const float* __restrict__ pts, const int32_t* __res
     xs[s] = make_float4(pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], 0.f);
 }
 
-// Per box: S_b, work-item count ceil(S_b / chunk) and the padded length of its
-// source list.  Validates the CSR (ascending ids in range, own box present).
-__global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ nbr_ptr,
-                           const int32_t* __restrict__ nbr_idx, int32_t nb, int64_t nnz, int chunk, int upper,
-                           int32_t* __restrict__ box_src, int32_t* __restrict__ list_len, int32_t* __restrict__ n_chunks, int32_t* __restrict__ padded, int32_t* __restrict__ maxes,
-                           unsigned int* __restrict__ status) {
+// Per target box: S_b, work-item count ceil(S_b / chunk) and the padded length
+// of its source list, and the size of the source box of its own cell (the
+// sources that can sit at r = 0 from one of its targets).  Validates the CSR
+// (ascending ids in range; a one-set structure lists each box itself, a two-set
+// structure's nbr_self must point into the list or be -1).
+__global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ src_box_ptr,
+                           int32_t nbs, const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr_idx,
+                           const int32_t* __restrict__ nbr_self, int32_t nb, int64_t nnz, int chunk, int upper,
+                           int32_t* __restrict__ box_src, int32_t* __restrict__ list_len,
+                           int32_t* __restrict__ n_chunks, int32_t* __restrict__ padded, int32_t* __restrict__ self_len,
+                           int32_t* __restrict__ maxes, unsigned int* __restrict__ status) {
     int32_t b = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (b >= nb) return;
     int32_t e0 = nbr_ptr[b], e1 = nbr_ptr[b + 1];
-    int64_t s = 0, self = -1, s_up = 0;
+    int64_t s = 0, s_up = 0;
+    int32_t self = -1, self_n = 0;
     bool ok = e0 >= 0 && e1 >= e0 && e1 <= nnz && e1 - e0 <= 27;
     if (ok) {
-        for (int32_t e = e0; e < e1; ++e) {
+        const int32_t want = nbr_self ? nbr_self[b] : -2;
+        if (nbr_self && (want < -1 || want >= e1 - e0)) ok = false;
+        for (int32_t e = e0; ok && e < e1; ++e) {
             int32_t c = nbr_idx[e];
-            if (c < 0 || c >= nb || (e > e0 && c <= nbr_idx[e - 1])) {
+            if (c < 0 || c >= nbs || (e > e0 && c <= nbr_idx[e - 1])) {
                 ok = false;
                 break;
             }
-            if (c == b) self = s;
-            s += box_ptr[c + 1] - box_ptr[c];
-            if (c >= b) s_up += box_ptr[c + 1] - box_ptr[c];
+            const int32_t sz = src_box_ptr[c + 1] - src_box_ptr[c];
+            if (nbr_self ? (e - e0 == want) : (c == b)) {
+                self = e - e0;
+                self_n = sz;
+            }
+            s += sz;
+            if (c >= b) s_up += sz;
         }
     }
     int32_t own = box_ptr[b + 1] - box_ptr[b];
-    if (!ok || self < 0 || own <= 0 || s > INT32_MAX - 4) {
+    if (!ok || (!nbr_self && self < 0) || own <= 0 || s > INT32_MAX - 4) {
         atomicOr(status, P2P_DEV_BAD_INPUT);
         s = 0;
         s_up = 0;
-        self = 0;
+        self_n = 0;
     }
     box_src[b] = (int32_t)s;
+    self_len[b] = self_n;
     const int64_t len = upper ? s_up : s;  // length of the box's source list
     list_len[b] = (int32_t)len;
     int32_t c = (int32_t)((len + chunk - 1) / chunk);
@@ -203,8 +228,9 @@ __global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* _
 // sources) first.
 __global__ void k_item_records(const int32_t* __restrict__ n_chunks, const int32_t* __restrict__ item_off,
                                const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ list_len,
-                               const int32_t* __restrict__ pk_off, int32_t nb, int chunk, int tg,
-                               ItemRec* __restrict__ recs, uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+                               const int32_t* __restrict__ self_len, const int32_t* __restrict__ pk_off, int32_t nb,
+                               int chunk, int tg, int two_sets, ItemRec* __restrict__ recs,
+                               uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
     int32_t b = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (b >= nb) return;
     const int32_t c = n_chunks[b], o = item_off[b];
@@ -217,7 +243,8 @@ __global__ void k_item_records(const int32_t* __restrict__ n_chunks, const int32
         r.ns = min(chunk, S - s0);
         r.tb = tb;
         r.nt = nt;
-        r.m_end = max(0, min(r.ns, nt - s0)) | (s0 == 0 ? (1 << 16) : 0);
+        // the own cell's sources lead the list; in a one-set plan they are the box's targets themselves
+        r.m_end = max(0, min(r.ns, self_len[b] - s0)) | ((s0 == 0 && !two_sets) ? (1 << 16) : 0);
         r.map_full = p2p_lane_map(min(nt, tg), r.ns);
         r.map_last = p2p_lane_map(last, r.ns);
         r.b = b;
@@ -269,26 +296,34 @@ __global__ void k_tc_list_fill(const int32_t* __restrict__ nbr_ptr, const int32_
     while (o < off[b + 1]) list[o++] = -1;
 }
 
-// One warp per box: writes the box's source list -- the box's own sources
-// first, then the other neighbour boxes in ascending id (the order the pair
-// kernel's r = 0 mask relies on) -- as box-sorted indices (nb_src, the index
-// arrays of the indexing method, Sec. 3.2) and, for the redundant layout, as a
-// copy of the coordinates plus original indices (the repetition of Sec. 3.3).
+// One warp per target box: writes the box's source list -- the sources of its
+// own cell first (the box itself in a one-set plan, the source box of the same
+// cell in a two-set plan), then the other neighbour boxes in ascending id (the
+// order the pair kernel's r = 0 mask relies on) -- as box-sorted source indices
+// (nb_src, the index arrays of the indexing method, Sec. 3.2) and, for the
+// redundant layout, as a copy of the coordinates plus original indices (the
+// repetition of Sec. 3.3).  xs, perm and box_ptr are the SOURCE side.
 __global__ void k_pack(const float4* __restrict__ xs, const int32_t* __restrict__ perm,
                        const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ nbr_ptr,
-                       const int32_t* __restrict__ nbr_idx, const int32_t* __restrict__ pk_off, int32_t nb, int upper,
-                       int32_t* __restrict__ nb_src, float4* __restrict__ pk_xyz, int32_t* __restrict__ pk_src) {
+                       const int32_t* __restrict__ nbr_idx, const int32_t* __restrict__ nbr_self,
+                       const int32_t* __restrict__ pk_off, int32_t nb, int upper, int32_t* __restrict__ nb_src,
+                       float4* __restrict__ pk_xyz, int32_t* __restrict__ pk_src) {
     const int lane = threadIdx.x & 31;
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
     const int32_t e0 = nbr_ptr[b];
     int32_t ne = nbr_ptr[b + 1] - e0;
     const int32_t c = lane < ne ? nbr_idx[e0 + lane] : -1;
-    const unsigned selfm = __ballot_sync(P2P_FULL_MASK, c == (int32_t)b);
-    const int sp = selfm ? __ffs(selfm) - 1 : 0;
-    // full list: slot 0 <- own box, slots 1..sp <- entries 0..sp-1, later slots unchanged;
+    int sp;
+    if (nbr_self) {
+        sp = nbr_self[b];  // -1: no source box in the own cell, the list keeps ascending order
+    } else {
+        const unsigned selfm = __ballot_sync(P2P_FULL_MASK, c == (int32_t)b);
+        sp = selfm ? __ffs(selfm) - 1 : 0;
+    }
+    // full list: slot 0 <- own cell, slots 1..sp <- entries 0..sp-1, later slots unchanged;
     // upper list (own box and higher ids only): slot i <- entry sp + i
-    int from = lane == 0 ? sp : (lane <= sp ? lane - 1 : lane);
+    int from = sp < 0 ? lane : (lane == 0 ? sp : (lane <= sp ? lane - 1 : lane));
     if (upper) {
         from = min(sp + lane, 31);
         ne -= sp;
@@ -335,19 +370,29 @@ __global__ void k_pack(const float4* __restrict__ xs, const int32_t* __restrict_
     }
 }
 
-// Pairs of box b: n_b * S_b minus the pairs inside b with identical coordinates.
-__global__ void k_pair_count(const float4* __restrict__ xs, const int32_t* __restrict__ box_ptr,
-                             const int32_t* __restrict__ box_src, int32_t nb, unsigned long long* __restrict__ out) {
+// Pairs of target box b: n_b * S_b minus the (target, source) pairs of its own
+// cell with identical coordinates (xt / box_ptr: targets; xs / src_box_ptr:
+// sources; self_len / nbr_self locate the own cell's source box).
+__global__ void k_pair_count(const float4* __restrict__ xt, const int32_t* __restrict__ box_ptr,
+                             const float4* __restrict__ xs, const int32_t* __restrict__ src_box_ptr,
+                             const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr_idx,
+                             const int32_t* __restrict__ nbr_self, const int32_t* __restrict__ box_src, int32_t nb,
+                             unsigned long long* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
     const int32_t t0 = box_ptr[b], t1 = box_ptr[b + 1];
+    int32_t c = (int32_t)b;
+    if (nbr_self) c = nbr_self[b] >= 0 ? nbr_idx[nbr_ptr[b] + nbr_self[b]] : -1;
     long long dup = 0;
-    for (int32_t i = t0 + lane; i < t1; i += 32) {
-        float4 a = xs[i];
-        for (int32_t j = t0; j < t1; ++j) {
-            float4 c = xs[j];
-            dup += (a.x == c.x && a.y == c.y && a.z == c.z) ? 1 : 0;
+    if (c >= 0) {
+        const int32_t s0 = src_box_ptr[c], s1 = src_box_ptr[c + 1];
+        for (int32_t i = t0 + lane; i < t1; i += 32) {
+            float4 a = xt[i];
+            for (int32_t j = s0; j < s1; ++j) {
+                float4 q = xs[j];
+                dup += (a.x == q.x && a.y == q.y && a.z == q.z) ? 1 : 0;
+            }
         }
     }
 #pragma unroll
@@ -356,6 +401,35 @@ __global__ void k_pair_count(const float4* __restrict__ xs, const int32_t* __res
         long long p = (long long)(t1 - t0) * (long long)box_src[b] - dup;
         atomicAdd(out, (unsigned long long)p);
     }
+}
+
+// Points (sorted position s) whose new coordinates fall in another grid cell
+// than the coordinates the plan holds (same cell rule as the binning), and
+// non-finite new coordinates.
+__global__ void k_moved(const float* __restrict__ pts, const int32_t* __restrict__ perm,
+                        const float4* __restrict__ xs, int64_t n, double lo0, double lo1, double lo2, double h, int ng,
+                        unsigned long long* __restrict__ moved, int32_t* __restrict__ bad) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t j = perm[s];
+    const float x = pts[3 * j], y = pts[3 * j + 1], z = pts[3 * j + 2];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
+        *bad = 1;
+        return;
+    }
+    const float4 o = xs[s];
+    if (cell_of(x, lo0, h, ng) != cell_of(o.x, lo0, h, ng) || cell_of(y, lo1, h, ng) != cell_of(o.y, lo1, h, ng) ||
+        cell_of(z, lo2, h, ng) != cell_of(o.z, lo2, h, ng))
+        atomicAdd(moved, 1ull);
+}
+
+// Redundant layout: the per-box copies of the listed source coordinates from the box-sorted ones.
+__global__ void k_repack_xyz(const float4* __restrict__ xs, const int32_t* __restrict__ nb_src, int64_t packed,
+                             float4* __restrict__ pk_xyz) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= packed) return;
+    const int32_t j = nb_src[p];
+    pk_xyz[p] = j >= 0 ? xs[j] : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 int ceil_log2(int v) {
@@ -432,7 +506,7 @@ p2p_tuning resolve_tuning(const p2p_tuning* t) {
 
 struct PlanLayout {
     p2p_plan p;  // pointers only
-    int32_t *n_chunks, *item_off, *padded, *maxes, *small, *list_len;
+    int32_t *n_chunks, *item_off, *padded, *maxes, *small, *list_len, *self_len;
     void* scan_ws;
     // item-sort scratch (aliases the strength staging buffer when it is large enough)
     ItemRec* recs;
@@ -442,41 +516,46 @@ struct PlanLayout {
     size_t bytes;
 };
 
-PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, int64_t nnz, p2p_layout layout, int32_t max_nrhs,
-                       const p2p_tuning& t, void* ws) {
+// Sizes of a plan: n targets in nb boxes, n_src sources in nbs boxes (two_sets), sources = sum of S_b.
+PlanLayout plan_layout(int64_t n, int32_t nb, int64_t n_src, int32_t nbs, bool two_sets, int64_t sources, int64_t nnz,
+                       p2p_layout layout, int32_t max_nrhs, const p2p_tuning& t, void* ws) {
     Carver c{static_cast<char*>(ws), 0, (size_t)-1};
     PlanLayout L;
     memset(&L.p, 0, sizeof(L.p));
     size_t m = (size_t)(n > 0 ? n : 1), mb = (size_t)(nb > 0 ? nb : 1);
+    size_t ms = (size_t)(n_src > 0 ? n_src : 1), mbs = (size_t)(nbs > 0 ? nbs : 1);
     const size_t max_items = (size_t)(sources / t.chunk) + mb + 1;
     const size_t list_bound = (size_t)sources + 3 * mb + 4;
     const bool red = layout == P2P_LAYOUT_REDUNDANT;
     L.p.status = c.take<unsigned int>(4);
     L.p.scratch64 = c.take<long long>(4);
     L.p.xs = c.take<float4>(m);
+    L.p.xs_src = two_sets ? c.take<float4>(ms) : L.p.xs;
     L.p.box_src = c.take<int32_t>(mb);
     L.p.items = c.take<ItemRec>(max_items);
     L.p.pk_off = c.take<int32_t>(mb + 1);
     L.p.nb_src = c.take<int32_t>(list_bound);
     L.p.pk_xyz = red ? c.take<float4>(list_bound) : nullptr;
     L.p.pk_src = red ? c.take<int32_t>(list_bound) : nullptr;
-    const size_t lam_rows = red ? (m > list_bound ? m : list_bound) : m;
+    const size_t lam_rows = red ? (ms > list_bound ? ms : list_bound) : ms;
     const size_t lam_bytes = lam_rows * (size_t)max_nrhs * sizeof(float2);
     L.p.lam_buf = c.take<float2>(lam_rows * (size_t)max_nrhs);
-    L.p.g_buf = c.take<float2>(m * (size_t)max_nrhs);
-    const size_t tc_bytes = p2p_tc_pack_bytes((int64_t)m, (int32_t)mb, max_nrhs);
-    L.p.tc_gstart = tc_bytes ? c.take<int32_t>(mb + 1) : nullptr;
+    L.p.g_buf = two_sets ? nullptr : c.take<float2>(m * (size_t)max_nrhs);
+    const size_t tc_bytes = p2p_tc_pack_bytes((int64_t)ms, (int32_t)mbs, max_nrhs);
+    L.p.tc_gstart = tc_bytes ? c.take<int32_t>(mbs + 1) : nullptr;
     L.p.tc_glist_off = tc_bytes ? c.take<int32_t>(mb + 1) : nullptr;
     L.p.tc_gcount = tc_bytes ? c.take<int32_t>(mb) : nullptr;
     L.p.tc_glist = tc_bytes ? c.take<int32_t>(p2p_tc_list_bound(sources, nnz, (int32_t)mb)) : nullptr;
     L.p.tc_pack = tc_bytes ? c.take<unsigned char>(tc_bytes) : nullptr;
-    L.n_chunks = c.take<int32_t>(mb);
+    const size_t mx = mb > mbs ? mb : mbs;
+    L.n_chunks = c.take<int32_t>(mx);
     L.list_len = c.take<int32_t>(mb);
+    L.self_len = c.take<int32_t>(mb);
     L.item_off = c.take<int32_t>(mb + 1);
     L.padded = c.take<int32_t>(mb);
     L.maxes = c.take<int32_t>(4);
     L.small = c.take<int32_t>(4);
-    L.scan_ws = c.take<char>(scan_workspace_bytes(nb));
+    L.scan_ws = c.take<char>(scan_workspace_bytes((int64_t)mx));
     // sort scratch: inside lam_buf if it fits, else after everything else
     Carver sc{reinterpret_cast<char*>(L.p.lam_buf), 0, lam_bytes};
     sc.take<ItemRec>(max_items);
@@ -497,6 +576,43 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t sources, int64_t nnz, p2p_
     return L;
 }
 
+// Everything a plan is made from: the target side (points, perm, boxes), the
+// source side (the same arrays for a one-set plan) and the target-to-source
+// neighbour CSR.
+struct PlanInput {
+    const float* pts;
+    int64_t n;
+    const int32_t* perm;
+    const int32_t* box_ptr;
+    int32_t nb;
+    const float* src_pts;
+    int64_t n_src;
+    const int32_t* src_perm;
+    const int32_t* src_box_ptr;
+    int32_t nbs;
+    const int32_t* nbr_ptr;
+    const int32_t* nbr_idx;
+    const int32_t* nbr_self;  // NULL for one-set plans
+    int64_t nnz;
+    int64_t sources;
+    bool two_sets;
+};
+
+p2p_status check_sizes(int64_t n, int32_t nb, int64_t n_src, int32_t nbs, int64_t sources, p2p_layout layout,
+                       int32_t max_nrhs, bool two_sets) {
+    if (n < 0 || n >= INT32_MAX || nb < 0 || nb > n || n_src < 0 || n_src >= INT32_MAX || nbs < 0 || nbs > n_src ||
+        sources < 0 || sources >= INT32_MAX || max_nrhs < 1 || max_nrhs > 256)
+        return P2P_ERR_INVALID;
+    if (layout != P2P_LAYOUT_INDEXED && layout != P2P_LAYOUT_REDUNDANT && layout != P2P_LAYOUT_SYMMETRIC)
+        return P2P_ERR_INVALID;
+    if (two_sets && layout == P2P_LAYOUT_SYMMETRIC) return P2P_ERR_UNSUPPORTED;
+    return P2P_OK;
+}
+
+p2p_status plan_create(p2p_plan** plan, const PlanInput& in, p2p_kernel kernel, float k, p2p_layout layout,
+                       int32_t max_nrhs, const p2p_tuning* tuning, void* workspace, size_t workspace_bytes,
+                       cudaStream_t s);
+
 }  // namespace
 
 // ===================================================================== C ABI ==
@@ -514,6 +630,7 @@ P2P_API const char* p2p_status_string(p2p_status s) {
         case P2P_ERR_TIMEOUT: return "device-side wait timed out";
         case P2P_ERR_UNSUPPORTED: return "unsupported";
         case P2P_ERR_ALLOC: return "host allocation failed";
+        case P2P_ERR_STALE: return "a point left its leaf box: rebuild the plan";
     }
     return "unknown status";
 }
@@ -572,11 +689,17 @@ P2P_API p2p_status p2p_neighbors_workspace_size(int32_t num_boxes, size_t* bytes
     return P2P_OK;
 }
 
-P2P_API p2p_status p2p_build_neighbors(const int64_t* box_keys, const int32_t* box_ptr, int32_t num_boxes,
-                                       int32_t ng, int32_t* nbr_ptr, int32_t* nbr_idx, int64_t* nnz,
-                                       int64_t* sources, void* work, size_t work_bytes, p2p_stream_t stream) {
-    if (num_boxes < 0 || ng < 1 || ng > (1 << 21) || !nbr_ptr || !nnz || !sources) return P2P_ERR_INVALID;
-    cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// Neighbour CSR of nb target boxes over nbs source boxes (the same boxes for a one-set structure).
+p2p_status build_neighbors(const int64_t* box_keys, int32_t num_boxes, const int64_t* src_keys,
+                           const int32_t* src_box_ptr, int32_t num_src, int32_t ng, int32_t* nbr_ptr,
+                           int32_t* nbr_idx, int32_t* nbr_self, int64_t* nnz, int64_t* sources, void* work,
+                           size_t work_bytes, cudaStream_t s, bool two) {
+    if (num_boxes < 0 || num_src < 0 || ng < 1 || ng > (1 << 21) || !nbr_ptr || !nnz || !sources)
+        return P2P_ERR_INVALID;
     *nnz = 0;
     *sources = 0;
     if (num_boxes == 0) {
@@ -584,20 +707,34 @@ P2P_API p2p_status p2p_build_neighbors(const int64_t* box_keys, const int32_t* b
         P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_build_neighbors");
         return P2P_OK;
     }
-    if (!box_keys || !box_ptr || !nbr_idx || !work || ((uintptr_t)work & 255)) return P2P_ERR_INVALID;
+    if (!box_keys || !src_keys || !src_box_ptr || !nbr_idx || !work || ((uintptr_t)work & 255)) return P2P_ERR_INVALID;
+    if (two && !nbr_self) return P2P_ERR_INVALID;
     if ((int64_t)num_boxes * 27 >= INT32_MAX) return P2P_ERR_UNSUPPORTED;
     NbrLayout L = nbr_layout(num_boxes, work);
     if (work_bytes < L.bytes) return P2P_ERR_WORKSPACE;
     P2P_TRY_CUDA(cudaMemsetAsync(L.bad, 0, 2 * sizeof(int32_t), s), "p2p_build_neighbors");
     P2P_TRY_CUDA(cudaMemsetAsync(L.sum, 0, sizeof(unsigned long long), s), "p2p_build_neighbors");
     const unsigned wblocks = blocks_for((int64_t)num_boxes * 32, kThreads);
-    k_neighbors<false><<<wblocks, kThreads, 0, s>>>(box_keys, box_ptr, num_boxes, ng, L.cnt, L.src_cnt, nullptr,
-                                                    nullptr, L.bad);
+    if (two) {
+        if (num_src > 1) {
+            k_keys_ascending<<<blocks_for(num_src, kThreads), kThreads, 0, s>>>(src_keys, num_src, L.bad);
+            P2P_CHECK_LAUNCH("p2p_build_neighbors_st/keys");
+        }
+        k_neighbors<false, true><<<wblocks, kThreads, 0, s>>>(box_keys, num_boxes, src_keys, num_src, src_box_ptr, ng,
+                                                              L.cnt, L.src_cnt, nullptr, nullptr, nullptr, L.bad);
+    } else {
+        k_neighbors<false, false><<<wblocks, kThreads, 0, s>>>(box_keys, num_boxes, src_keys, num_src, src_box_ptr, ng,
+                                                               L.cnt, L.src_cnt, nullptr, nullptr, nullptr, L.bad);
+    }
     P2P_CHECK_LAUNCH("p2p_build_neighbors/count");
     P2P_TRY_CUDA(scan_exclusive_i32(L.cnt, nbr_ptr, num_boxes, nbr_ptr + num_boxes, L.scan_ws, s),
                  "p2p_build_neighbors/scan");
-    k_neighbors<true><<<wblocks, kThreads, 0, s>>>(box_keys, box_ptr, num_boxes, ng, nullptr, nullptr, nbr_ptr,
-                                                   nbr_idx, L.bad);
+    if (two)
+        k_neighbors<true, true><<<wblocks, kThreads, 0, s>>>(box_keys, num_boxes, src_keys, num_src, src_box_ptr, ng,
+                                                             nullptr, nullptr, nbr_ptr, nbr_idx, nbr_self, L.bad);
+    else
+        k_neighbors<true, false><<<wblocks, kThreads, 0, s>>>(box_keys, num_boxes, src_keys, num_src, src_box_ptr, ng,
+                                                              nullptr, nullptr, nbr_ptr, nbr_idx, nullptr, L.bad);
     P2P_CHECK_LAUNCH("p2p_build_neighbors/fill");
     k_sum_i32<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(L.src_cnt, num_boxes, L.sum);
     P2P_CHECK_LAUNCH("p2p_build_neighbors/sum");
@@ -614,57 +751,56 @@ P2P_API p2p_status p2p_build_neighbors(const int64_t* box_keys, const int32_t* b
     return P2P_OK;
 }
 
-P2P_API p2p_status p2p_plan_workspace_size(int64_t n, int32_t num_boxes, int64_t nnz, int64_t sources,
-                                           p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
-                                           size_t* bytes) {
-    (void)nnz;
-    if (!bytes || n < 0 || n >= INT32_MAX || num_boxes < 0 || num_boxes > n || sources < 0 ||
-        sources >= INT32_MAX || max_nrhs < 1 || max_nrhs > 256 ||
-        (layout != P2P_LAYOUT_INDEXED && layout != P2P_LAYOUT_REDUNDANT && layout != P2P_LAYOUT_SYMMETRIC))
-        return P2P_ERR_INVALID;
-    p2p_tuning t = resolve_tuning(tuning);
-    if (!tuning_valid(t)) return P2P_ERR_INVALID;
-    *bytes = plan_layout(n, num_boxes, sources, nnz, layout, max_nrhs, t, nullptr).bytes;
-    return P2P_OK;
-}
-
-P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n, const int32_t* perm,
-                                   const int32_t* box_ptr, int32_t num_boxes, const int32_t* nbr_ptr,
-                                   const int32_t* nbr_idx, int64_t nnz, int64_t sources, p2p_kernel kernel, float k,
-                                   p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning, void* workspace,
-                                   size_t workspace_bytes, p2p_stream_t stream) {
+p2p_status plan_create(p2p_plan** plan, const PlanInput& in, p2p_kernel kernel, float k, p2p_layout layout,
+                       int32_t max_nrhs, const p2p_tuning* tuning, void* workspace, size_t workspace_bytes,
+                       cudaStream_t s) {
     if (!plan) return P2P_ERR_INVALID;
     *plan = nullptr;
-    size_t need = 0;
-    p2p_status st = p2p_plan_workspace_size(n, num_boxes, nnz, sources, layout, max_nrhs, tuning, &need);
+    p2p_status st = check_sizes(in.n, in.nb, in.n_src, in.nbs, in.sources, layout, max_nrhs, in.two_sets);
     if (st != P2P_OK) return st;
+    p2p_tuning t = resolve_tuning(tuning);
+    if (!tuning_valid(t)) return P2P_ERR_INVALID;
+    const int32_t nb = in.nb;
+    const int64_t n = in.n;
     if (kernel != P2P_HELMHOLTZ && kernel != P2P_LAPLACE) return P2P_ERR_INVALID;
     if (!isfinite(k)) return P2P_ERR_INVALID;
-    if ((n > 0 && num_boxes < 1) || (n == 0 && num_boxes != 0)) return P2P_ERR_INVALID;
-    if (nnz < num_boxes || nnz > 27ll * num_boxes) return P2P_ERR_INVALID;
-    if (n > 0 && (!pts || !perm || !box_ptr || !nbr_ptr || !nbr_idx)) return P2P_ERR_INVALID;
-    if (!workspace || ((uintptr_t)workspace & 255) || ((uintptr_t)pts & 3)) return P2P_ERR_INVALID;
-    if (workspace_bytes < need) return P2P_ERR_WORKSPACE;
-    cudaStream_t s = (cudaStream_t)stream;
-    p2p_tuning t = resolve_tuning(tuning);
-    PlanLayout L = plan_layout(n, num_boxes, sources, nnz, layout, max_nrhs, t, workspace);
+    if ((n > 0 && nb < 1) || (n == 0 && nb != 0)) return P2P_ERR_INVALID;
+    if ((in.n_src > 0 && in.nbs < 1) || (in.n_src == 0 && in.nbs != 0)) return P2P_ERR_INVALID;
+    if (in.two_sets ? (in.nnz < 0 || in.nnz > 27ll * nb) : (in.nnz < nb || in.nnz > 27ll * nb))
+        return P2P_ERR_INVALID;
+    if (n > 0 && (!in.pts || !in.perm || !in.box_ptr || !in.nbr_ptr || (in.nnz > 0 && !in.nbr_idx)))
+        return P2P_ERR_INVALID;
+    if (in.two_sets && n > 0 && (!in.nbr_self || (in.n_src > 0 && (!in.src_pts || !in.src_perm || !in.src_box_ptr))))
+        return P2P_ERR_INVALID;
+    if (!workspace || ((uintptr_t)workspace & 255) || ((uintptr_t)in.pts & 3) || ((uintptr_t)in.src_pts & 3))
+        return P2P_ERR_INVALID;
+    PlanLayout L = plan_layout(n, nb, in.n_src, in.nbs, in.two_sets, in.sources, in.nnz, layout, max_nrhs, t,
+                               workspace);
+    if (workspace_bytes < L.bytes) return P2P_ERR_WORKSPACE;
     p2p_plan* p = (p2p_plan*)malloc(sizeof(p2p_plan));
     if (!p) return P2P_ERR_ALLOC;
     *p = L.p;
     p->n = n;
-    p->nb = num_boxes;
-    p->nnz = nnz;
-    p->sources = sources;
+    p->nb = nb;
+    p->two_sets = in.two_sets ? 1 : 0;
+    p->n_src = in.n_src;
+    p->nbs = in.nbs;
+    p->nnz = in.nnz;
+    p->sources = in.sources;
     p->kernel = kernel;
     p->k = kernel == P2P_LAPLACE ? 0.f : k;
     p->layout = layout;
     p->max_nrhs = max_nrhs;
     p->tune = t;
-    p->pts = pts;
-    p->perm = perm;
-    p->box_ptr = box_ptr;
-    p->nbr_ptr = nbr_ptr;
-    p->nbr_idx = nbr_idx;
+    p->pts = in.pts;
+    p->perm = in.perm;
+    p->box_ptr = in.box_ptr;
+    p->nbr_ptr = in.nbr_ptr;
+    p->nbr_idx = in.nbr_idx;
+    p->src_pts = in.src_pts;
+    p->src_perm = in.src_perm;
+    p->src_box_ptr = in.src_box_ptr;
+    p->nbr_self = in.two_sets ? in.nbr_self : nullptr;
     p->n_items = 0;
     p->max_chunks = 0;
     p->max_box = 0;
@@ -685,13 +821,21 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
         return P2P_OK;
     }
     FAIL_CUDA(cudaMemsetAsync(L.maxes, 0, 4 * sizeof(int32_t), s), "p2p_plan_create");
-    k_gather_xyz<<<blocks_for(n, kThreads), kThreads, 0, s>>>(pts, perm, n, p->xs);
+    k_gather_xyz<<<blocks_for(n, kThreads), kThreads, 0, s>>>(in.pts, in.perm, n, p->xs);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/gather");
+    if (in.two_sets && in.n_src > 0) {
+        k_gather_xyz<<<blocks_for(in.n_src, kThreads), kThreads, 0, s>>>(in.src_pts, in.src_perm, in.n_src, p->xs_src);
+        FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/gather_sources");
+    }
     const int upper = layout == P2P_LAYOUT_SYMMETRIC;
-    k_box_info<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(box_ptr, nbr_ptr, nbr_idx, num_boxes, nnz,
-                                                                     t.chunk, upper, p->box_src, L.list_len,
-                                                                     L.n_chunks, L.padded, L.maxes, p->status);
-    FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/box_info");
+    auto box_info = [&]() {
+        k_box_info<<<blocks_for(nb, kThreads), kThreads, 0, s>>>(in.box_ptr, p->src_box_ptr, p->nbs, in.nbr_ptr,
+                                                                 in.nbr_idx, p->nbr_self, nb, in.nnz, t.chunk, upper,
+                                                                 p->box_src, L.list_len, L.n_chunks, L.padded,
+                                                                 L.self_len, L.maxes, p->status);
+        return cudaGetLastError();
+    };
+    FAIL_CUDA(box_info(), "p2p_plan_create/box_info");
     if (tuning_is_auto(tuning)) {
         // When most source lists hold just over one default chunk (193 .. 256 sources), every box would get a
         // full item and a short tail item with the same fixed cost; 256-source items (6 warps per block, so two
@@ -700,40 +844,39 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
         int32_t tails = 0;
         FAIL_CUDA(cudaMemcpyAsync(&tails, L.maxes + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
         FAIL_CUDA(cudaStreamSynchronize(s), "p2p_plan_create");
-        if (2ll * tails > num_boxes) {
+        if (2ll * tails > nb) {
             t.chunk = kWideTuning.chunk;
             t.warps_per_cta = kWideTuning.warps_per_cta;
             p->tune = t;
             FAIL_CUDA(cudaMemsetAsync(L.maxes, 0, 4 * sizeof(int32_t), s), "p2p_plan_create");
-            k_box_info<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(box_ptr, nbr_ptr, nbr_idx, num_boxes, nnz,
-                                                                             t.chunk, upper, p->box_src, L.list_len,
-                                                                             L.n_chunks, L.padded, L.maxes, p->status);
-            FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/box_info");
+            FAIL_CUDA(box_info(), "p2p_plan_create/box_info");
         }
     }
-    FAIL_CUDA(scan_exclusive_i32(L.n_chunks, L.item_off, num_boxes, L.small, L.scan_ws, s), "p2p_plan_create/scan");
-    FAIL_CUDA(scan_exclusive_i32(L.padded, p->pk_off, num_boxes, p->pk_off + num_boxes, L.scan_ws, s),
+    FAIL_CUDA(scan_exclusive_i32(L.n_chunks, L.item_off, nb, L.small, L.scan_ws, s), "p2p_plan_create/scan");
+    FAIL_CUDA(scan_exclusive_i32(L.padded, p->pk_off, nb, p->pk_off + nb, L.scan_ws, s),
               "p2p_plan_create/scan_lists");
-    k_pack<<<blocks_for((int64_t)num_boxes * 32, kThreads), kThreads, 0, s>>>(
-        p->xs, perm, box_ptr, nbr_ptr, nbr_idx, p->pk_off, num_boxes, upper, p->nb_src, p->pk_xyz, p->pk_src);
+    k_pack<<<blocks_for((int64_t)nb * 32, kThreads), kThreads, 0, s>>>(p->xs_src, p->src_perm, p->src_box_ptr,
+                                                                      in.nbr_ptr, in.nbr_idx, p->nbr_self, p->pk_off,
+                                                                      nb, upper, p->nb_src, p->pk_xyz, p->pk_src);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/pack");
-    k_item_records<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(L.n_chunks, L.item_off, box_ptr, L.list_len,
-                                                                        p->pk_off, num_boxes, t.chunk, t.target_group,
-                                                                        L.recs, L.keys, L.vals);
+    k_item_records<<<blocks_for(nb, kThreads), kThreads, 0, s>>>(L.n_chunks, L.item_off, in.box_ptr, L.list_len,
+                                                                 L.self_len, p->pk_off, nb, t.chunk, t.target_group,
+                                                                 p->two_sets, L.recs, L.keys, L.vals);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/items");
-    if (p->tc_gstart) {
-        // 16-source groups of the tensor-core path (n_chunks is free once the items are built)
-        k_tc_groups<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(box_ptr, num_boxes, L.n_chunks);
+    if (p->tc_gstart && p->nbs > 0) {
+        // 16-source groups of the tensor-core path over the source boxes (n_chunks is free once the items are
+        // built), then every target box's list of its neighbourhood's groups
+        k_tc_groups<<<blocks_for(p->nbs, kThreads), kThreads, 0, s>>>(p->src_box_ptr, p->nbs, L.n_chunks);
         FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/tc_groups");
-        FAIL_CUDA(scan_exclusive_i32(L.n_chunks, p->tc_gstart, num_boxes, p->tc_gstart + num_boxes, L.scan_ws, s),
+        FAIL_CUDA(scan_exclusive_i32(L.n_chunks, p->tc_gstart, p->nbs, p->tc_gstart + p->nbs, L.scan_ws, s),
                   "p2p_plan_create/tc_scan");
-        k_tc_list_len<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(nbr_ptr, nbr_idx, p->tc_gstart, num_boxes,
-                                                                            p->tc_gcount, L.n_chunks);
+        k_tc_list_len<<<blocks_for(nb, kThreads), kThreads, 0, s>>>(in.nbr_ptr, in.nbr_idx, p->tc_gstart, nb,
+                                                                    p->tc_gcount, L.n_chunks);
         FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/tc_lists");
-        FAIL_CUDA(scan_exclusive_i32(L.n_chunks, p->tc_glist_off, num_boxes, p->tc_glist_off + num_boxes, L.scan_ws, s),
+        FAIL_CUDA(scan_exclusive_i32(L.n_chunks, p->tc_glist_off, nb, p->tc_glist_off + nb, L.scan_ws, s),
                   "p2p_plan_create/tc_scan");
-        k_tc_list_fill<<<blocks_for(num_boxes, kThreads), kThreads, 0, s>>>(nbr_ptr, nbr_idx, p->tc_gstart,
-                                                                             p->tc_glist_off, num_boxes, p->tc_glist);
+        k_tc_list_fill<<<blocks_for(nb, kThreads), kThreads, 0, s>>>(in.nbr_ptr, in.nbr_idx, p->tc_gstart,
+                                                                     p->tc_glist_off, nb, p->tc_glist);
         FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/tc_lists");
     }
     int32_t host[4] = {0, 0, 0, 0};
@@ -743,10 +886,10 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
     FAIL_CUDA(cudaMemcpyAsync(host, L.maxes, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
     FAIL_CUDA(cudaMemcpyAsync(host + 2, L.small, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
     FAIL_CUDA(cudaMemcpyAsync(&status, p->status, sizeof(status), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
-    FAIL_CUDA(cudaMemcpyAsync(&packed, p->pk_off + num_boxes, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+    FAIL_CUDA(cudaMemcpyAsync(&packed, p->pk_off + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
               "p2p_plan_create");
-    if (p->tc_gstart)
-        FAIL_CUDA(cudaMemcpyAsync(&tc_groups, p->tc_gstart + num_boxes, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+    if (p->tc_gstart && p->nbs > 0)
+        FAIL_CUDA(cudaMemcpyAsync(&tc_groups, p->tc_gstart + p->nbs, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
                   "p2p_plan_create");
     FAIL_CUDA(cudaStreamSynchronize(s), "p2p_plan_create");
     if (!status) {
@@ -776,6 +919,87 @@ P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n,
     return P2P_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+P2P_API p2p_status p2p_build_neighbors(const int64_t* box_keys, const int32_t* box_ptr, int32_t num_boxes,
+                                       int32_t ng, int32_t* nbr_ptr, int32_t* nbr_idx, int64_t* nnz,
+                                       int64_t* sources, void* work, size_t work_bytes, p2p_stream_t stream) {
+    return build_neighbors(box_keys, num_boxes, box_keys, box_ptr, num_boxes, ng, nbr_ptr, nbr_idx, nullptr, nnz,
+                           sources, work, work_bytes, (cudaStream_t)stream, false);
+}
+
+P2P_API p2p_status p2p_build_neighbors_st(const int64_t* tgt_keys, int32_t num_tgt_boxes, const int64_t* src_keys,
+                                          const int32_t* src_box_ptr, int32_t num_src_boxes, int32_t ng,
+                                          int32_t* nbr_ptr, int32_t* nbr_idx, int32_t* nbr_self, int64_t* nnz,
+                                          int64_t* sources, void* work, size_t work_bytes, p2p_stream_t stream) {
+    if (num_src_boxes == 0 && num_tgt_boxes > 0) {
+        // no sources: every list is empty
+        if (!nbr_ptr || !nbr_self || !nnz || !sources) return P2P_ERR_INVALID;
+        cudaStream_t s = (cudaStream_t)stream;
+        *nnz = 0;
+        *sources = 0;
+        P2P_TRY_CUDA(cudaMemsetAsync(nbr_ptr, 0, sizeof(int32_t) * ((size_t)num_tgt_boxes + 1), s),
+                     "p2p_build_neighbors_st");
+        P2P_TRY_CUDA(cudaMemsetAsync(nbr_self, 0xff, sizeof(int32_t) * (size_t)num_tgt_boxes, s),
+                     "p2p_build_neighbors_st");
+        P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_build_neighbors_st");
+        return P2P_OK;
+    }
+    return build_neighbors(tgt_keys, num_tgt_boxes, src_keys, src_box_ptr, num_src_boxes, ng, nbr_ptr, nbr_idx,
+                           nbr_self, nnz, sources, work, work_bytes, (cudaStream_t)stream, true);
+}
+
+P2P_API p2p_status p2p_plan_workspace_size(int64_t n, int32_t num_boxes, int64_t nnz, int64_t sources,
+                                           p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
+                                           size_t* bytes) {
+    if (!bytes) return P2P_ERR_INVALID;
+    p2p_status st = check_sizes(n, num_boxes, n, num_boxes, sources, layout, max_nrhs, false);
+    if (st != P2P_OK) return st;
+    p2p_tuning t = resolve_tuning(tuning);
+    if (!tuning_valid(t)) return P2P_ERR_INVALID;
+    *bytes = plan_layout(n, num_boxes, n, num_boxes, false, sources, nnz, layout, max_nrhs, t, nullptr).bytes;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_plan_workspace_size_st(int64_t n_tgt, int32_t num_tgt_boxes, int64_t n_src,
+                                              int32_t num_src_boxes, int64_t nnz, int64_t sources, p2p_layout layout,
+                                              int32_t max_nrhs, const p2p_tuning* tuning, size_t* bytes) {
+    if (!bytes) return P2P_ERR_INVALID;
+    p2p_status st = check_sizes(n_tgt, num_tgt_boxes, n_src, num_src_boxes, sources, layout, max_nrhs, true);
+    if (st != P2P_OK) return st;
+    p2p_tuning t = resolve_tuning(tuning);
+    if (!tuning_valid(t)) return P2P_ERR_INVALID;
+    *bytes = plan_layout(n_tgt, num_tgt_boxes, n_src, num_src_boxes, true, sources, nnz, layout, max_nrhs, t, nullptr)
+                 .bytes;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n, const int32_t* perm,
+                                   const int32_t* box_ptr, int32_t num_boxes, const int32_t* nbr_ptr,
+                                   const int32_t* nbr_idx, int64_t nnz, int64_t sources, p2p_kernel kernel, float k,
+                                   p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning, void* workspace,
+                                   size_t workspace_bytes, p2p_stream_t stream) {
+    PlanInput in{pts, n, perm, box_ptr, num_boxes, pts, n, perm, box_ptr, num_boxes, nbr_ptr, nbr_idx, nullptr,
+                 nnz, sources, false};
+    return plan_create(plan, in, kernel, k, layout, max_nrhs, tuning, workspace, workspace_bytes,
+                       (cudaStream_t)stream);
+}
+
+P2P_API p2p_status p2p_plan_create_st(p2p_plan** plan, const float* tgt_pts, int64_t n_tgt, const int32_t* tgt_perm,
+                                      const int32_t* tgt_box_ptr, int32_t num_tgt_boxes, const float* src_pts,
+                                      int64_t n_src, const int32_t* src_perm, const int32_t* src_box_ptr,
+                                      int32_t num_src_boxes, const int32_t* nbr_ptr, const int32_t* nbr_idx,
+                                      const int32_t* nbr_self, int64_t nnz, int64_t sources, p2p_kernel kernel,
+                                      float k, p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
+                                      void* workspace, size_t workspace_bytes, p2p_stream_t stream) {
+    PlanInput in{tgt_pts, n_tgt, tgt_perm, tgt_box_ptr, num_tgt_boxes, src_pts, n_src, src_perm, src_box_ptr,
+                 num_src_boxes, nbr_ptr, nbr_idx, nbr_self, nnz, sources, true};
+    return plan_create(plan, in, kernel, k, layout, max_nrhs, tuning, workspace, workspace_bytes,
+                       (cudaStream_t)stream);
+}
+
 P2P_API p2p_status p2p_plan_destroy(p2p_plan* plan) {
     free(plan);
     return P2P_OK;
@@ -800,12 +1024,48 @@ P2P_API p2p_status p2p_plan_pair_count(const p2p_plan* plan, int64_t* pairs, p2p
     cudaStream_t s = (cudaStream_t)stream;
     P2P_TRY_CUDA(cudaMemsetAsync(plan->scratch64, 0, sizeof(long long), s), "p2p_plan_pair_count");
     k_pair_count<<<blocks_for((int64_t)plan->nb * 32, kThreads), kThreads, 0, s>>>(
-        plan->xs, plan->box_ptr, plan->box_src, plan->nb, (unsigned long long*)plan->scratch64);
+        plan->xs, plan->box_ptr, plan->xs_src, plan->src_box_ptr, plan->nbr_ptr, plan->nbr_idx, plan->nbr_self,
+        plan->box_src, plan->nb, (unsigned long long*)plan->scratch64);
     P2P_CHECK_LAUNCH("p2p_plan_pair_count");
     long long v = 0;
     P2P_TRY_CUDA(cudaMemcpyAsync(&v, plan->scratch64, sizeof(v), cudaMemcpyDeviceToHost, s), "p2p_plan_pair_count");
     P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_plan_pair_count");
     *pairs = v;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_plan_update_points(p2p_plan* plan, const float* pts, const double lo[3], double h, int32_t ng,
+                                          int64_t* moved, p2p_stream_t stream) {
+    if (moved) *moved = 0;
+    if (!plan || !lo || !(h > 0.0) || !isfinite(h) || ng < 1 || ng > (1 << 21)) return P2P_ERR_INVALID;
+    if (!isfinite(lo[0]) || !isfinite(lo[1]) || !isfinite(lo[2])) return P2P_ERR_INVALID;
+    if (plan->two_sets) return P2P_ERR_UNSUPPORTED;
+    if (plan->n == 0) return P2P_OK;
+    if (!pts || ((uintptr_t)pts & 3)) return P2P_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    // scratch64[0]: moved count, scratch64[1]: non-finite flag (the pair count's slot, free between calls)
+    P2P_TRY_CUDA(cudaMemsetAsync(plan->scratch64, 0, 2 * sizeof(long long), s), "p2p_plan_update_points");
+    k_moved<<<blocks_for(plan->n, kThreads), kThreads, 0, s>>>(pts, plan->perm, plan->xs, plan->n, lo[0], lo[1], lo[2],
+                                                               h, ng, (unsigned long long*)plan->scratch64,
+                                                               (int32_t*)(plan->scratch64 + 1));
+    P2P_CHECK_LAUNCH("p2p_plan_update_points/check");
+    long long host[2] = {0, 0};
+    P2P_TRY_CUDA(cudaMemcpyAsync(host, plan->scratch64, sizeof(host), cudaMemcpyDeviceToHost, s),
+                 "p2p_plan_update_points");
+    P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_plan_update_points");
+    if (host[1]) return P2P_ERR_INVALID;
+    if (moved) *moved = host[0];
+    if (host[0]) return P2P_ERR_STALE;
+    k_gather_xyz<<<blocks_for(plan->n, kThreads), kThreads, 0, s>>>(pts, plan->perm, plan->n, plan->xs);
+    P2P_CHECK_LAUNCH("p2p_plan_update_points/gather");
+    if (plan->pk_xyz && plan->packed > 0) {
+        k_repack_xyz<<<blocks_for(plan->packed, kThreads), kThreads, 0, s>>>(plan->xs, plan->nb_src, plan->packed,
+                                                                             plan->pk_xyz);
+        P2P_CHECK_LAUNCH("p2p_plan_update_points/repack");
+    }
+    plan->pts = pts;
+    plan->src_pts = pts;
+    P2P_TRY_CUDA(cudaStreamSynchronize(s), "p2p_plan_update_points");
     return P2P_OK;
 }
 

@@ -663,7 +663,9 @@ __device__ void run_epilogue(const TcArgs& a, const TcSmem& sm, uint32_t tmem, i
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         int b, t0, nt;
         unit_of(a, u, b, t0, nt);
-        if (nt == 0) continue;
+        // a box without any source group (two point sets, no source nearby) has no stages and no accumulator:
+        // the producer skips it too, and its results stay at the zeros written before the launch
+        if (nt == 0 || a.gcount[b] == 0) continue;
         // sets with work in this unit: entries 0 .. gcount - 1 of the list go to sets 0, 1, 2, 3, 0, ...
         const int used = min(kSets, a.gcount[b]);
         const int T = (nt + 7) & ~7;
@@ -894,8 +896,9 @@ p2p_status p2p_tc_stage(const p2p_plan* plan, const float2* lam, int32_t nrhs, i
     if (plan->n == 0 || plan->tc_groups == 0) return P2P_OK;
     const int rb_count = (nrhs + 63) / 64;
     dim3 grid((unsigned)plan->tc_groups, (unsigned)rb_count);
-    k_tc_pack<<<grid, 128, 0, s>>>(lam, ld, nrhs, plan->perm, plan->box_ptr, plan->xs, plan->tc_gstart, plan->nb,
-                                   rb_count, plan->tc_pack);
+    // the group records are built over the SOURCE boxes
+    k_tc_pack<<<grid, 128, 0, s>>>(lam, ld, nrhs, plan->src_perm, plan->src_box_ptr, plan->xs_src, plan->tc_gstart,
+                                   plan->nbs, rb_count, plan->tc_pack);
     P2P_CHECK_LAUNCH("p2p_apply_stage/tc_pack");
     return P2P_OK;
 }
