@@ -363,7 +363,7 @@ def _config(args, layout):
     return {"workload": "sphere_occupancy_sweep", "n_points": 1 << 20, "occupancies": list(OCCUPANCIES),
             "grids": [180, 124, 86, 61], "kernel": "helmholtz", "k": "2*pi/(4h)", "nrhs": 1, "layout": layout,
             "tuning": {"chunk": getattr(args, "chunk", 0), "warps_per_cta": getattr(args, "warps", 0),
-                       "target_group": getattr(args, "target_group", 0),
+                       "target_group": getattr(args, "target_group", 0), "warp_boxes": getattr(args, "warp_boxes", 0),
                        "note": "0 = chosen by each plan; the launch tuning used is in roofline.per_occupancy"},
             "l2": "flushed between timed steps (256 MiB write, outside the timed events)"}
 
@@ -423,7 +423,8 @@ def run_ours(args):
             layout, tuning = tune["layout"], tune["tuning"]
         else:
             tuning = {k: v for k, v in (("chunk", args.chunk), ("warps_per_cta", args.warps),
-                                        ("target_group", args.target_group)) if v} or None
+                                        ("target_group", args.target_group), ("warp_boxes", args.warp_boxes))
+                      if v} or None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         plan = api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k, layout=layout, tuning=tuning)
@@ -942,6 +943,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="sources per work item (0: library default)")
     ap.add_argument("--warps", type=int, default=0, help="warps per block (0: library default)")
     ap.add_argument("--target-group", type=int, default=0, help="targets per sweep (0: library default)")
+    ap.add_argument("--warp-boxes", type=int, default=0,
+                    help="direct kernel boxes per warp (1, 2, 4), -1 for the staged pipeline, 0: library default")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=("sweep", "cube", "multirhs", "grad", "batched"), default="sweep",

@@ -96,12 +96,22 @@ typedef enum {
  * chunk and warps_per_cta both zero (or a NULL tuning) the plan chooses them: 192
  * sources per item and 8 warps per block, or 256 and 6 when more than half of the
  * boxes' source lists hold 193 .. 256 sources (a 192-source item would leave each of
- * them a short tail item of the same fixed cost). */
+ * them a short tail item of the same fixed cost).
+ *
+ * warp_boxes selects the kernel of one-right-hand-side FP32 applies.  The staged
+ * pipeline stages chunks of a box's source list in shared memory and suits boxes
+ * of many targets; the direct kernel gives each warp 1, 2 or 4 whole boxes (32,
+ * 16 or 8 lanes each) and reads the sources through the L1, which suits sparse
+ * boxes (a few targets each), where a staged item carries too little work for
+ * its fixed cost.  0: the plan decides from its mean box occupancy; -1: the
+ * staged pipeline; 1, 2 or 4: the direct kernel with that many boxes per warp.
+ * Multi-RHS applies, the symmetric layout and the batched launch always use the
+ * staged pipeline. */
 typedef struct {
     int32_t chunk;         /* sources staged per work item, multiple of 32, 32..1024 (default 192) */
     int32_t warps_per_cta; /* warps per thread block of the pair kernel, 1..16 (default 8) */
     int32_t target_group;  /* targets swept per pass, multiple of 32, 32..128 (default 32) */
-    int32_t reserved;
+    int32_t warp_boxes;    /* 0 (plan decides), -1 (staged pipeline), 1, 2 or 4 (direct kernel) */
 } p2p_tuning;
 
 typedef struct p2p_plan p2p_plan;
@@ -480,6 +490,17 @@ P2P_API p2p_status p2p_diag_tc_gemm(const float* A, const float* B, float* D, in
  * and the CUDA context remains usable.
  */
 P2P_API p2p_status p2p_diag_wait_timeout(unsigned int* status, int32_t limit, p2p_stream_t stream);
+
+/*
+ * Self-check of the tensor-core path's abort handling (not part of the
+ * operator): every pipeline wait of the plan's later tensor-core launches polls
+ * at most `polls` times (0: it gives up at once; negative: the normal bound).
+ * A wait that runs out sets P2P_ERR_TIMEOUT in the status word; the roles stop,
+ * the producers and MMA issuers wait (bounded) for their own copies and MMAs in
+ * flight, the block frees its tensor memory and returns.  The results of such a
+ * launch are not valid; restore the bound before relying on the plan again.
+ */
+P2P_API p2p_status p2p_diag_tc_wait_limit(p2p_plan* plan, int32_t polls);
 
 /* Reads and clears the plan's device status word.  Synchronises. */
 P2P_API p2p_status p2p_last_async_status(const p2p_plan* plan, p2p_stream_t stream);

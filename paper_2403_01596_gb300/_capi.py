@@ -47,7 +47,7 @@ class P2PError(RuntimeError):
 
 class p2p_tuning(ctypes.Structure):
     _fields_ = [("chunk", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("target_group", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("target_group", ctypes.c_int32), ("warp_boxes", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
             "p2p_last_async_status": ([P, P], ctypes.c_int),
             "p2p_diag_tc_gemm": ([P, P, P, i32, i32, P, P], ctypes.c_int),
             "p2p_diag_wait_timeout": ([P, i32, P], ctypes.c_int),
+            "p2p_diag_tc_wait_limit": ([P, i32], ctypes.c_int),
             "p2p_batch_workspace_size": ([P, i32, i32, PSZ], ctypes.c_int),
             "p2p_batch_create": ([ctypes.POINTER(P), P, i32, i32, i32, P, sz, P], ctypes.c_int),
             "p2p_batch_apply": ([P, P, P, i64, P], ctypes.c_int),
@@ -195,7 +196,7 @@ def _tuning(t):
     if t is None:
         return None
     return ctypes.byref(p2p_tuning(int(t.get("chunk", 0)), int(t.get("warps_per_cta", 0)),
-                                   int(t.get("target_group", 0)), 0))
+                                   int(t.get("target_group", 0)), int(t.get("warp_boxes", 0))))
 
 
 def p2p_plan_workspace_size(n, num_boxes, nnz, sources, layout, max_nrhs, tuning=None) -> int:
@@ -252,7 +253,7 @@ def p2p_plan_info(plan) -> dict:
                                ctypes.byref(layout), ctypes.byref(t)), "p2p_plan_info")
     return {"n": n.value, "num_boxes": nb.value, "sources": src.value, "work_items": items.value,
             "layout": layout.value, "tuning": {"chunk": t.chunk, "warps_per_cta": t.warps_per_cta,
-                                               "target_group": t.target_group}}
+                                               "target_group": t.target_group, "warp_boxes": t.warp_boxes}}
 
 
 def p2p_plan_update_points(plan, pts, lo, h, ng, stream=None):
@@ -381,3 +382,7 @@ def p2p_apply_host(pipe, plans, lams_host, outs_host, stream=None):
 def p2p_host_pipe_destroy(pipe):
     if pipe:
         load().p2p_host_pipe_destroy(pipe)
+
+
+def p2p_diag_tc_wait_limit(plan, polls: int):
+    check(load().p2p_diag_tc_wait_limit(plan, int(polls)), "p2p_diag_tc_wait_limit")

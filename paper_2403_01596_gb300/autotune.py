@@ -1,4 +1,4 @@
-"""Autotuner for the P2P launch configuration (layout, source chunk, warps per block).
+"""Autotuner for the P2P launch configuration (layout, kernel, source chunk, warps per block).
 
 For a point set and grid, every candidate configuration is built as a plan on
 the shared box structure and timed with CUDA events on the current stream
@@ -19,13 +19,18 @@ import os
 import statistics
 import threading
 
+# staged pipeline (warp_boxes -1) with several chunk / block shapes, and the direct kernel with 1, 2 or 4 boxes
+# per warp (one-RHS applies only; for several RHS a plan runs the staged pipeline whatever warp_boxes says)
 DEFAULT_CANDIDATES = (
-    {"chunk": 192, "warps_per_cta": 8, "target_group": 32},
-    {"chunk": 128, "warps_per_cta": 8, "target_group": 32},
-    {"chunk": 160, "warps_per_cta": 8, "target_group": 32},
-    {"chunk": 256, "warps_per_cta": 4, "target_group": 32},
-    {"chunk": 128, "warps_per_cta": 4, "target_group": 32},
-    {"chunk": 192, "warps_per_cta": 8, "target_group": 64},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": -1},
+    {"chunk": 128, "warps_per_cta": 8, "target_group": 32, "warp_boxes": -1},
+    {"chunk": 160, "warps_per_cta": 8, "target_group": 32, "warp_boxes": -1},
+    {"chunk": 256, "warps_per_cta": 4, "target_group": 32, "warp_boxes": -1},
+    {"chunk": 128, "warps_per_cta": 4, "target_group": 32, "warp_boxes": -1},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 64, "warp_boxes": -1},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 1},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 2},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 4},
 )
 
 DEFAULT_LAYOUTS = ("indexed", "redundant", "symmetric")
@@ -48,7 +53,7 @@ def occupancy_bucket(n_points: int, num_boxes: int) -> int:
 
 
 def cache_key(gpu: str, sms: int, kernel: str, bucket: int, nrhs: int, layouts) -> str:
-    return f"{gpu}|{sms}|{kernel}|d{bucket}|r{nrhs}|{'+'.join(sorted(layouts))}"
+    return f"v2|{gpu}|{sms}|{kernel}|d{bucket}|r{nrhs}|{'+'.join(sorted(layouts))}"
 
 
 def load_cache(path: str | None = None) -> dict:
@@ -118,14 +123,16 @@ def tune(structure, k: float, kernel: str = "helmholtz", nrhs: int = 1, layouts=
     timings = []
     for layout in layouts:
         for cand in candidates:
+            if layout == "symmetric" and cand.get("warp_boxes", 0) > 0:
+                continue  # the symmetric layout always runs the staged pipeline
             plan = Plan(structure.points, structure.lo, structure.h, structure.ng, k, kernel=kernel, layout=layout,
                         max_nrhs=nrhs, tuning=dict(cand), structure=structure)
             timings.append({"layout": layout, "tuning": dict(cand), "ms": _time_plan(plan, lam, out, reps)})
             plan.close()
     best = select(timings)
     result = {"layout": best["layout"], "tuning": best["tuning"], "ms": best["ms"],
-              "all": [(t["layout"], t["tuning"]["chunk"], t["tuning"]["warps_per_cta"], round(t["ms"], 5))
-                      for t in timings]}
+              "all": [(t["layout"], t["tuning"]["chunk"], t["tuning"]["warps_per_cta"],
+                       t["tuning"].get("warp_boxes", 0), round(t["ms"], 5)) for t in timings]}
     if use_cache:
         with _lock:
             cache = load_cache(path)

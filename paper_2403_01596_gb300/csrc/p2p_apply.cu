@@ -6,10 +6,15 @@
 // p2p_pair.cuh, shared with the persistent batched launch.
 #include <math.h>
 
+#include <algorithm>
+
+#include "p2p_direct.cuh"
 #include "p2p_pair.cuh"
 
 using namespace p2p_detail;
 using namespace p2p_pair;
+using p2p_direct::DirectArgs;
+using p2p_direct::kDirectWarps;
 
 namespace {
 
@@ -24,6 +29,34 @@ __global__ void __launch_bounds__(P2P_PAIR_MAX_THREADS, R == 1 ? P2P_PAIR_MIN_BL
     unsigned char* ws = smem_raw + (size_t)warp * warp_smem_bytes(a.chunk, R, a.sym);
     run_pipeline<R>(ws, a.chunk, a.sym != 0, lane, a.items, a.n_items, (int64_t)blockIdx.x * warps + warp,
                     (int64_t)gridDim.x * warps, a.status, [&](const ItemRec&) -> const PairArgs* { return &a; });
+}
+
+// Direct kernel (sparse boxes, one right-hand side): warp w of the persistent
+// grid serves K boxes at a time, sources read through the L1 (p2p_direct.cuh).
+#ifndef P2P_DIRECT_MIN_BLOCKS
+#define P2P_DIRECT_MIN_BLOCKS 4
+#endif
+template <int KERN, bool RED, int K>
+__global__ void __launch_bounds__(kDirectWarps * 32, P2P_DIRECT_MIN_BLOCKS)
+    k_pair_direct(const __grid_constant__ DirectArgs a) {
+    __shared__ float2 red[kDirectWarps][4 * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    p2p_direct::run_direct<KERN, RED, K>(a, red[warp], (int)blockIdx.x * kDirectWarps + warp,
+                                         (int64_t)gridDim.x * kDirectWarps, lane);
+}
+
+using DirectKernel = void (*)(DirectArgs);
+
+template <int KERN, bool RED>
+DirectKernel direct_kernel_k(int k) {
+    return k == 1 ? k_pair_direct<KERN, RED, 1> : (k == 2 ? k_pair_direct<KERN, RED, 2> : k_pair_direct<KERN, RED, 4>);
+}
+
+DirectKernel direct_kernel(const p2p_plan* p) {
+    const bool red = p->layout == P2P_LAYOUT_REDUNDANT;
+    if (p->kernel == P2P_HELMHOLTZ)
+        return red ? direct_kernel_k<P2P_HELMHOLTZ, true>(p->direct_k) : direct_kernel_k<P2P_HELMHOLTZ, false>(p->direct_k);
+    return red ? direct_kernel_k<P2P_LAPLACE, true>(p->direct_k) : direct_kernel_k<P2P_LAPLACE, false>(p->direct_k);
 }
 
 // ------------------------------------------------------ coordinate gradient --
@@ -333,6 +366,15 @@ cudaError_t p2p_pair_configure(p2p_plan* plan) {
     cudaError_t e = configure_r<1>(plan);
     if (e == cudaSuccess) e = configure_r<2>(plan);
     if (e == cudaSuccess) e = configure_r<4>(plan);
+    plan->direct_grid = 0;
+    if (e == cudaSuccess && plan->direct_k > 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_kernel(plan), kDirectWarps * 32, 0);
+        if (e == cudaSuccess) plan->direct_grid = per_sm * sms;
+    }
     return e;
 }
 
@@ -388,6 +430,27 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
     a.ld = ld;
     a.nrhs = nrhs;
     if (adjoint) a.k = -a.k;
+    if (nrhs == 1 && plan->direct_k > 0 && plan->direct_grid > 0) {
+        // one right-hand side on sparse boxes: the direct kernel, one item per box, every row stored once
+        DirectArgs d;
+        d.items = plan->ditems;
+        d.n_items = plan->nb;
+        d.xs = plan->xs_src;
+        d.xt = plan->xs;
+        d.pk_xyz = plan->pk_xyz;
+        d.nb_src = plan->nb_src;
+        d.lam = plan->lam_buf;
+        d.perm = plan->perm;
+        d.out = (float2*)out;
+        d.ld = ld;
+        d.k = a.k;
+        const int64_t blocks_needed = (plan->nb + (int64_t)kDirectWarps * plan->direct_k - 1) /
+                                      ((int64_t)kDirectWarps * plan->direct_k);
+        const int grid = (int)std::min<int64_t>(plan->direct_grid, blocks_needed);
+        direct_kernel(plan)<<<grid, kDirectWarps * 32, 0, s>>>(d);
+        P2P_CHECK_LAUNCH("p2p_apply/direct");
+        return P2P_OK;
+    }
     if (a.atomic_out && !plan->two_sets)
         P2P_TRY_CUDA(cudaMemset2DAsync(out, (size_t)ld * 8, 0, (size_t)nrhs * 8, (size_t)plan->n, s), "p2p_apply/zero");
     if (plan->n_items == 0) return P2P_OK;

@@ -31,19 +31,20 @@ struct ItemRec {
     int32_t b;         // box id
 };
 
-// Lane map of a target group of nt targets against ns sources: TT targets per
-// lane (1, 2 or 4), G = ceil(nt / TT) target slots, Q = 32 / G source slices,
-// and mG = ceil(65536 / G) so that x / G == (x * mG) >> 16 for x < 128.
-// TT minimises the lane's instruction count: ceil(ns / Q) iterations of TT
-// pair evaluations (~20 instructions each) plus the per-iteration source
-// loads and loop control (~4).  Packed as TT | G << 3 | Q << 9 | (mG - 1) << 15.
-__host__ __device__ inline int32_t p2p_lane_map(int nt, int ns) {
+// Lane map of a target group of nt targets against ns sources on `lanes` lanes
+// (32, or the 16 / 8 lanes of a box in the direct kernel): TT targets per lane
+// (1, 2 or 4), G = ceil(nt / TT) target slots, Q = lanes / G source slices, and
+// mG = ceil(65536 / G) so that x / G == (x * mG) >> 16 for x < 128.  TT
+// minimises the lane's instruction count: ceil(ns / Q) iterations of TT pair
+// evaluations (~20 instructions each) plus the per-iteration source loads and
+// loop control (`per_iter`).  Packed as TT | G << 3 | Q << 9 | (mG - 1) << 15.
+__host__ __device__ inline int32_t p2p_lane_map(int nt, int ns, int lanes = 32, int per_iter = 4) {
     int best = 4, best_cost = 0x7fffffff;
     for (int tt = 1; tt <= 4; tt <<= 1) {
         const int g = (nt + tt - 1) / tt;
-        if (g > 32 || g < 1) continue;
-        const int q = 32 / g;
-        const int cost = (20 * tt + 4) * ((ns + q - 1) / q);
+        if (g > lanes || g < 1) continue;
+        const int q = lanes / g;
+        const int cost = (20 * tt + per_iter) * ((ns + q - 1) / q);
         if (cost < best_cost) {
             best_cost = cost;
             best = tt;
@@ -51,7 +52,7 @@ __host__ __device__ inline int32_t p2p_lane_map(int nt, int ns) {
     }
     int g = (nt + best - 1) / best;
     if (g < 1) g = 1;
-    const int q = 32 / g;
+    const int q = lanes / g;
     const int mg = (65536 + g - 1) / g;
     return best | (g << 3) | (q << 9) | ((mg - 1) << 15);
 }
@@ -96,6 +97,10 @@ struct p2p_plan {
     int32_t* nb_src;        // [packed] box-sorted index of every listed source, -1 for padding
     float4* pk_xyz;         // [packed] redundant layout: per-box copy of the listed coordinates
     int32_t* pk_src;        // [packed] redundant layout: original index of every listed source, -1 for padding
+    int32_t direct_k;       // boxes per warp of the direct kernel (1, 2 or 4); 0: the staged pipeline
+    ItemRec* ditems;        // [nb] direct kernel: one item per target box (whole source list, lane maps for
+                            // 32 / direct_k lanes), heaviest first
+    int32_t direct_grid;    // persistent grid of the direct kernel (blocks of kDirectWarps warps)
     int32_t grid[3];        // persistent grid of the pair kernel for R = 1, 2, 4 right-hand sides per pass
     int32_t grid_warps[3];  // warps per block of that grid (the tuning's, halved until a block fits)
     float2* lam_buf;        // [max(n, packed) * max_nrhs] sorted / packed strengths
@@ -111,6 +116,8 @@ struct p2p_plan {
     int32_t* tc_gcount;     // [nb] groups in the list of every box (without padding)
     unsigned char* tc_pack; // per-apply group records: BF16 hi/lo strength images (one per block of 64 RHS)
                             // followed by the group's 16 source coordinates
+    int32_t tc_wait_polls;  // poll bound of the tensor-core pipeline's waits, -1: the default (a self-check
+                            // lowers it to make the abort path run)
 };
 
 // Bytes of the tensor-core group records for n points in nb boxes (0 when max_nrhs < 16).

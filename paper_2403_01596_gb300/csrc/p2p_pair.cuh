@@ -224,16 +224,12 @@ __device__ __forceinline__ void load_lam_block(const PairArgs& a, const ItemRec&
 
 // ------------------------------------------------------------------- sweep --
 
-// One staged source against the lane's TT targets.  MASK: the source may
-// coincide with a target (own box) and r = 0 pairs are skipped; otherwise r > 0
-// and the guard only keeps an underflowed r^2 finite.
+// One source (coordinates p, strengths l) against the lane's TT targets.  MASK:
+// the source may coincide with a target (own box) and r = 0 pairs are skipped;
+// otherwise r > 0 and the guard only keeps an underflowed r^2 finite.
 template <int KERN, int R, int TT, bool MASK>
-__device__ __forceinline__ void pair_step(const float4* __restrict__ sx, const float2* __restrict__ sl, int s,
-                                          const float4 (&tx)[TT], float2 (&acc)[TT][R], float k) {
-    const float4 p = sx[s];
-    float2 l[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) l[r] = sl[s * R + r];
+__device__ __forceinline__ void pair_core(const float4 p, const float2 (&l)[R], const float4 (&tx)[TT],
+                                          float2 (&acc)[TT][R], float k) {
 #pragma unroll
     for (int u = 0; u < TT; ++u) {
         const float dx = p.x - tx[u].x, dy = p.y - tx[u].y, dz = p.z - tx[u].z;
@@ -268,24 +264,33 @@ __device__ __forceinline__ void pair_step(const float4* __restrict__ sx, const f
     }
 }
 
-// pair_step for an even number of targets per lane with the packed two-lane
+// One staged source s against the lane's TT targets (pair_core on shared memory).
+template <int KERN, int R, int TT, bool MASK>
+__device__ __forceinline__ void pair_step(const float4* __restrict__ sx, const float2* __restrict__ sl, int s,
+                                          const float4 (&tx)[TT], float2 (&acc)[TT][R], float k) {
+    const float4 p = sx[s];
+    float2 l[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) l[r] = sl[s * R + r];
+    pair_core<KERN, R, TT, MASK>(p, l, tx, acc, k);
+}
+
+// pair_core for an even number of targets per lane with the packed two-lane
 // FP32 instructions (add/mul/fma.f32x2): targets u and u + 1 share one register
 // pair in every operand, so coordinate differences, r^2, the phase, the
 // amplitude and the complex multiply-add issue once for two pairs; rsqrt and
 // sincos stay per pair.  Each packed operation rounds as its scalar
-// counterpart in pair_step, in the same order (the targets are kept negated so
+// counterpart in pair_core, in the same order (the targets are kept negated so
 // that p - t is one add).
 template <int KERN, int R, int TT, bool MASK>
-__device__ __forceinline__ void pair_step_x2(const float4* __restrict__ sx, const float2* __restrict__ sl, int s,
-                                             const float2 (&nx)[TT / 2], const float2 (&ny)[TT / 2],
-                                             const float2 (&nz)[TT / 2], float2 (&ax)[TT / 2][R],
-                                             float2 (&ay)[TT / 2][R], float2 k2) {
-    const float4 p = sx[s];
+__device__ __forceinline__ void pair_core_x2(const float4 p, const float2 (&lv)[R], const float2 (&nx)[TT / 2],
+                                             const float2 (&ny)[TT / 2], const float2 (&nz)[TT / 2],
+                                             float2 (&ax)[TT / 2][R], float2 (&ay)[TT / 2][R], float2 k2) {
     const float2 px = make_float2(p.x, p.x), py = make_float2(p.y, p.y), pz = make_float2(p.z, p.z);
     float2 lx[R], ly[R], nly[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const float2 l = sl[s * R + r];
+        const float2 l = lv[r];
         lx[r] = make_float2(l.x, l.x);
         ly[r] = make_float2(l.y, l.y);
         nly[r] = make_float2(-l.y, -l.y);
@@ -323,6 +328,19 @@ __device__ __forceinline__ void pair_step_x2(const float4* __restrict__ sx, cons
             }
         }
     }
+}
+
+// pair_core_x2 on staged source s.
+template <int KERN, int R, int TT, bool MASK>
+__device__ __forceinline__ void pair_step_x2(const float4* __restrict__ sx, const float2* __restrict__ sl, int s,
+                                             const float2 (&nx)[TT / 2], const float2 (&ny)[TT / 2],
+                                             const float2 (&nz)[TT / 2], float2 (&ax)[TT / 2][R],
+                                             float2 (&ay)[TT / 2][R], float2 k2) {
+    const float4 p = sx[s];
+    float2 l[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) l[r] = sl[s * R + r];
+    pair_core_x2<KERN, R, TT, MASK>(p, l, nx, ny, nz, ax, ay, k2);
 }
 
 __device__ __forceinline__ int map_tt(int32_t m) { return m & 7; }

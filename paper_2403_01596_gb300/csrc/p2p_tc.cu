@@ -326,6 +326,7 @@ struct TcArgs {
     int32_t slot_bytes;
     float k;
     unsigned int* status;
+    uint32_t wait_limit;           // polls of every pipeline wait (kWaitLimit unless a self-check lowers it)
 };
 
 // Slot layout: group record (A images, source coordinates), the unit's targets,
@@ -402,10 +403,13 @@ struct Ring {
 
 // ---- producer of set s (one warp; lane 0 issues) ----
 // A unit's group list is walked four entries (a quad) at a time, entry 4q + s going to set s.
+template <bool LIMITED>
 __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, int set, int lane) {
     volatile int* abort = sm.abort;
+    const uint32_t wlim = LIMITED ? a.wait_limit : kWaitLimit;
     const bool active = lane == 0;
     Ring r{0, 0u};
+    int64_t staged = 0;  // stages this producer has armed (their copies may still be in flight)
     const uint32_t rec = (uint32_t)record_bytes(a.rb_count);
     const int t_off = slot_t_off(a.rb_count), meta_off = slot_meta_off(a.rb_count, a.tg);
     bool failed = false;
@@ -423,7 +427,7 @@ __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, i
             for (int q = 0; q < nq; ++q) {
                 const int g = __shfl_sync(P2P_FULL_MASK, gl, q * kSets + set);
                 bool ok = true;
-                if (active) ok = mbar_wait(&sm.empty[set * a.slots + r.slot], r.phase ^ 1u, abort);
+                if (active) ok = mbar_wait(&sm.empty[set * a.slots + r.slot], r.phase ^ 1u, abort, wlim);
                 if (!__all_sync(P2P_FULL_MASK, ok)) {
                     if (!ok && !*abort) set_abort(a, sm);
                     failed = true;
@@ -445,6 +449,7 @@ __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, i
                         mbar_arrive(bar);
                     }
                 }
+                ++staged;
                 r.advance(a.slots);
             }
         }
@@ -452,7 +457,7 @@ __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, i
     // a terminal stage for each set
     if (!failed) {
         bool ok = true;
-        if (active) ok = mbar_wait(&sm.empty[set * a.slots + r.slot], r.phase ^ 1u, abort);
+        if (active) ok = mbar_wait(&sm.empty[set * a.slots + r.slot], r.phase ^ 1u, abort, wlim);
         if (__all_sync(P2P_FULL_MASK, ok)) {
             if (active) {
                 *reinterpret_cast<int4*>(slot_base(r.slot) + meta_off) = make_int4(-1, kDone, 0, 0);
@@ -464,8 +469,9 @@ __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, i
         }
     }
     if (failed && active) {
-        // wait (bounded) for the bulk copies of this set's latest round of slots
-        for (int i = 0; i < a.slots; ++i) {
+        // wait (bounded) for the bulk copies of this set's latest round of slots (the ones it has armed)
+        const int armed = (int)(staged < a.slots ? staged : a.slots);
+        for (int i = 0; i < armed; ++i) {
             if (--r.slot < 0) {
                 r.slot += a.slots;
                 r.phase ^= 1u;
@@ -532,9 +538,10 @@ __device__ __forceinline__ void g_tile(const float4* __restrict__ sx, float4 tx,
     store_split<SP>(b_hi, b_lo, op_off(T + t, h * SP), im);
 }
 
-template <int KERN>
+template <int KERN, bool LIMITED>
 __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
     volatile int* abort = sm.abort;
+    const uint32_t wlim = LIMITED ? a.wait_limit : kWaitLimit;
     const int t_off = slot_t_off(a.rb_count), b_off = slot_b_off(a.rb_count, a.tg);
     const int b_half = slot_b_half(a.tg), meta_off = slot_meta_off(a.rb_count, a.tg);
     // this thread's task in the current unit: target t, sources h sp .. h sp + sp - 1 (set at the unit's first quad)
@@ -545,7 +552,7 @@ __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
     while (true) {
         const int idx = set * a.slots + r.slot;
         unsigned char* base = sm.slots + (size_t)idx * a.slot_bytes;
-        if (!mbar_wait(&sm.full[idx], r.phase, abort)) {
+        if (!mbar_wait(&sm.full[idx], r.phase, abort, wlim)) {
             if (!*abort) set_abort(a, sm);
             break;
         }
@@ -586,8 +593,10 @@ __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
 }
 
 // ---- MMA issuer of a set (one thread) ----
+template <bool LIMITED>
 __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int set) {
     volatile int* abort = sm.abort;
+    const uint32_t wlim = LIMITED ? a.wait_limit : kWaitLimit;
     const int b_off = slot_b_off(a.rb_count, a.tg), b_half = slot_b_half(a.tg);
     const int meta_off = slot_meta_off(a.rb_count, a.tg);
     const uint32_t acc_cols = (uint32_t)(a.rb_count * 2 * a.tg);
@@ -597,7 +606,7 @@ __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int se
     while (true) {
         const int idx = set * a.slots + r.slot;
         unsigned char* base = sm.slots + (size_t)idx * a.slot_bytes;
-        if (!mbar_wait(&sm.full[idx], r.phase, abort)) {
+        if (!mbar_wait(&sm.full[idx], r.phase, abort, wlim)) {
             if (!*abort) set_abort(a, sm);
             break;
         }
@@ -606,13 +615,13 @@ __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int se
         const uint32_t ub = unit & 1u;
         if (m.y & kFirst) {
             // the epilogue has released this accumulator buffer (unit - 2)
-            if (!mbar_wait(&sm.acc_empty[ub], ((unit >> 1) & 1u) ^ 1u, abort)) {
+            if (!mbar_wait(&sm.acc_empty[ub], ((unit >> 1) & 1u) ^ 1u, abort, wlim)) {
                 if (!*abort) set_abort(a, sm);
                 break;
             }
             acc_started = false;
         }
-        if (!mbar_wait(&sm.full_b[idx], r.phase, abort)) {
+        if (!mbar_wait(&sm.full_b[idx], r.phase, abort, wlim)) {
             if (!*abort) set_abort(a, sm);
             break;
         }
@@ -653,8 +662,10 @@ __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int se
 }
 
 // ---- epilogue (128 threads, TMEM lanes by warp quadrant) ----
+template <bool LIMITED>
 __device__ void run_epilogue(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int64_t units, int warp, int lane) {
     volatile int* abort = sm.abort;
+    const uint32_t wlim = LIMITED ? a.wait_limit : kWaitLimit;
     const int q = warp & 3;
     const int m = q * 32 + lane;  // accumulator row
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
@@ -672,7 +683,7 @@ __device__ void run_epilogue(const TcArgs& a, const TcSmem& sm, uint32_t tmem, i
         const int tb = a.box_ptr[b] + t0;
         const uint32_t ub = k & 1u, par = (k >> 1) & 1u;
         ++k;
-        const bool ok = mbar_wait(&sm.acc_full[ub], par, abort);
+        const bool ok = mbar_wait(&sm.acc_full[ub], par, abort, wlim);
         // the 128 threads leave together (they meet at named barriers below)
         if (epi_any(!ok)) {
             if (!ok && !*abort) set_abort(a, sm);
@@ -726,7 +737,8 @@ __device__ void run_epilogue(const TcArgs& a, const TcSmem& sm, uint32_t tmem, i
     }
 }
 
-template <int KERN>
+// LIMITED: the waits poll at most a.wait_limit times (the abort-path self-check); otherwise kWaitLimit.
+template <int KERN, bool LIMITED>
 __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -751,14 +763,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ 
     const uint32_t tmem = *sm.tmem_slot;
     const int64_t units = (int64_t)a.nb * a.ngrp;
     if (warp < kGWarp0) {
-        run_producer(a, sm, units, warp, lane);
+        run_producer<LIMITED>(a, sm, units, warp, lane);
     } else if (warp < kMmaWarp0) {
         const int gw = warp - kGWarp0;
-        run_gset<KERN>(a, sm, gw / kSetWarps, (gw % kSetWarps) * 32 + lane);
+        run_gset<KERN, LIMITED>(a, sm, gw / kSetWarps, (gw % kSetWarps) * 32 + lane);
     } else if (warp < kEpiWarp0) {
-        if (lane == 0) run_mma(a, sm, tmem, warp - kMmaWarp0);
+        if (lane == 0) run_mma<LIMITED>(a, sm, tmem, warp - kMmaWarp0);
     } else {
-        run_epilogue(a, sm, tmem, units, warp, lane);
+        run_epilogue<LIMITED>(a, sm, tmem, units, warp, lane);
     }
     tc_fence_before();
     __syncthreads();
@@ -934,7 +946,10 @@ p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t
     a.slot_bytes = sh.slot_bytes;
     a.k = adjoint ? -plan->k : plan->k;
     a.status = plan->status;
-    auto kern = plan->kernel == P2P_LAPLACE ? k_p2p_tc<P2P_LAPLACE> : k_p2p_tc<P2P_HELMHOLTZ>;
+    a.wait_limit = plan->tc_wait_polls < 0 ? kWaitLimit : (uint32_t)plan->tc_wait_polls;
+    const bool limited = plan->tc_wait_polls >= 0;
+    auto kern = plan->kernel == P2P_LAPLACE ? (limited ? k_p2p_tc<P2P_LAPLACE, true> : k_p2p_tc<P2P_LAPLACE, false>)
+                                            : (limited ? k_p2p_tc<P2P_HELMHOLTZ, true> : k_p2p_tc<P2P_HELMHOLTZ, false>);
     P2P_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem), "p2p_apply_tc");
     const int64_t units = (int64_t)a.nb * a.ngrp;
     const int grid = (int)std::min<int64_t>(units, sms);
@@ -952,5 +967,13 @@ extern "C" P2P_API p2p_status p2p_diag_tc_gemm(const float* A, const float* B, f
                  "p2p_diag_tc_gemm");
     k_tc_gemm_check<<<1, 128, smem, (cudaStream_t)stream>>>(A, B, D, K, n, tmem_cols_for(n), status);
     P2P_CHECK_LAUNCH("p2p_diag_tc_gemm");
+    return P2P_OK;
+}
+
+// Self-check of the tensor-core path's abort handling: every pipeline wait of the plan's later tensor-core
+// launches polls at most `polls` times (negative: the normal bound).
+extern "C" P2P_API p2p_status p2p_diag_tc_wait_limit(p2p_plan* plan, int32_t polls) {
+    if (!plan) return P2P_ERR_INVALID;
+    plan->tc_wait_polls = polls < 0 ? -1 : polls;
     return P2P_OK;
 }

@@ -19,8 +19,10 @@ def test_autotune_picks_caches_and_is_correct(tmp_path):
     st = api.BoxStructure(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng)
     first = autotune.tune(st, wl.k, reps=3, path=cache)
     assert not first["cached"]
-    assert len(first["all"]) == len(autotune.DEFAULT_LAYOUTS) * len(autotune.DEFAULT_CANDIDATES)
-    assert first["ms"] == min(t[3] for t in first["all"]) or first["ms"] > 0
+    # every (layout, candidate) but the direct-kernel candidates of the symmetric layout, which runs staged
+    direct = sum(1 for c in autotune.DEFAULT_CANDIDATES if c.get("warp_boxes", 0) > 0)
+    assert len(first["all"]) == len(autotune.DEFAULT_LAYOUTS) * len(autotune.DEFAULT_CANDIDATES) - direct
+    assert abs(first["ms"] - min(t[4] for t in first["all"])) <= 1e-5  # "all" keeps 5 decimals
     again = autotune.tune(st, wl.k, reps=3, path=cache)
     assert again["cached"] and again["layout"] == first["layout"] and again["tuning"] == first["tuning"]
     plan = api.Plan(st.points, wl.lo, wl.h, wl.ng, wl.k, layout=first["layout"], tuning=first["tuning"],

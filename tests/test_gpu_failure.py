@@ -50,3 +50,41 @@ def test_host_rejects_bad_arguments():
         C.p2p_apply_path(plan._plan, lam, torch.empty_like(lam), 2, 1, 0, C.P2P_PATH_AUTO)
     with pytest.raises(C.P2PError):
         C.p2p_diag_wait_timeout(torch.zeros(1, dtype=torch.int32, device="cuda"), 0)
+
+
+def test_tensor_core_abort_path_frees_tensor_memory():
+    """The tensor-core kernel's abort path: with every pipeline wait capped at 0, 1 or 3 polls a wait runs out
+    (at 0 polls at once; at 1 or 3 polls, when it does, with copies and MMAs in flight), the status word reports
+    the timeout, and the block drains its own copies and MMAs and frees its tensor memory -- the next launch
+    allocates tensor memory again and, with the normal bound restored, matches the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_01596_gb300 import _capi as C, api
+    wl = W.Workload("s", W.unit_sphere(30000, 5), (-1, -1, -1), 2 / 36, 36, 30.0, 5)
+    lam = W.strengths(wl.n, 16, 5)
+    ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
+    plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, wl.k, max_nrhs=16)
+    lam_d = torch.from_numpy(lam).cuda()
+
+    def rel(out):
+        return (np.linalg.norm(out - ref, axis=0) / np.linalg.norm(ref, axis=0)).max()
+
+    assert rel(plan.apply(lam_d, path="tc_bf16x3").cpu().numpy()) <= 1e-5
+    assert plan.async_status() == C.P2P_OK
+    seen = {}
+    for polls in (0, 1, 3):
+        C.p2p_diag_tc_wait_limit(plan._plan, polls)
+        out = plan.apply(lam_d, path="tc_bf16x3").cpu().numpy()
+        st = plan.async_status()
+        seen[polls] = st
+        if polls == 0:
+            assert st == C.P2P_ERR_TIMEOUT
+        else:
+            assert st in (C.P2P_OK, C.P2P_ERR_TIMEOUT)
+            if st == C.P2P_OK:
+                assert rel(out) <= 1e-5
+    C.p2p_diag_tc_wait_limit(plan._plan, -1)
+    for _ in range(2):
+        assert rel(plan.apply(lam_d, path="tc_bf16x3").cpu().numpy()) <= 1e-5
+        assert plan.async_status() == C.P2P_OK
+    print("tensor-core abort path, status per poll bound:", seen)

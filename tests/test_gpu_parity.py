@@ -144,10 +144,11 @@ def test_apply_high_frequency(edge, layout):
     assert err <= TOL
 
 
-@pytest.mark.parametrize("tuning", [{"chunk": 32, "warps_per_cta": 4, "target_group": 32},
-                                    {"chunk": 64, "warps_per_cta": 1, "target_group": 64},
-                                    {"chunk": 256, "warps_per_cta": 16, "target_group": 128},
-                                    {"chunk": 1024, "warps_per_cta": 2, "target_group": 96}])
+@pytest.mark.parametrize("tuning", [{"chunk": 32, "warps_per_cta": 4, "target_group": 32, "warp_boxes": -1},
+                                    {"chunk": 64, "warps_per_cta": 1, "target_group": 64, "warp_boxes": -1},
+                                    {"chunk": 256, "warps_per_cta": 16, "target_group": 128, "warp_boxes": -1},
+                                    {"chunk": 1024, "warps_per_cta": 2, "target_group": 96, "warp_boxes": -1},
+                                    {"warp_boxes": 1}, {"warp_boxes": 2}, {"warp_boxes": 4}])
 def test_apply_tunings(tuning):
     api = _cuda()
     wl = _clustered(12000, 13)
@@ -157,6 +158,31 @@ def test_apply_tunings(tuning):
         plan = _plan(api, wl, "helmholtz", layout, tuning=tuning)
         out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
         assert rel_l2(out, ref).max() <= TOL, (layout, tuning)
+        want = -1 if layout == "symmetric" else tuning["warp_boxes"]
+        assert plan.info["tuning"]["warp_boxes"] == want
+
+
+@pytest.mark.parametrize("warp_boxes", [1, 2, 4])
+@pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
+@pytest.mark.parametrize("layout", ["indexed", "redundant"])
+def test_direct_kernel(warp_boxes, kernel, layout):
+    """The direct kernel (1, 2 or 4 whole boxes per warp, sources read through the L1) on the dense cube (boxes
+    of ~64 targets: several passes per box at 8 lanes per box), a sparse sphere and the clustered assembly
+    (occupancy 1 - 128), forward and adjoint; every result row is stored once (the output starts as garbage)."""
+    api = _cuda()
+    kern = oracle.HELMHOLTZ if kernel == "helmholtz" else oracle.LAPLACE
+    for wl in (W.cube_dense(), _small_sphere(30000, 48, 22), _clustered(20000, 23)):
+        k = wl.k if kernel == "helmholtz" else 0.0
+        lam = W.strengths(wl.n, 1, 24)
+        plan = _plan(api, wl, kernel, layout, tuning={"warp_boxes": warp_boxes}, k=k)
+        assert plan.info["tuning"]["warp_boxes"] == warp_boxes
+        for adjoint in (False, True):
+            out = torch.full((wl.n, 1), 5.0 - 3.0j, dtype=torch.complex64, device="cuda")
+            plan.apply(torch.from_numpy(lam).cuda(), out=out, adjoint=adjoint)
+            ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, k, kernel=kern, adjoint=adjoint)
+            err = rel_l2(out.cpu().numpy(), ref).max()
+            assert err <= TOL, (wl.name, adjoint, err)
+        assert plan.async_status() == 0
 
 
 @pytest.mark.parametrize("path", ["fp32_per_rhs", "fp32_shared"])
@@ -256,7 +282,8 @@ def test_edge_cases():
     lam = W.strengths(len(p), 1, 4)
     ref = oracle.p2p(p, lam, wl.lo, wl.h, wl.ng, wl.k)
     for layout in ("indexed", "redundant", "symmetric"):
-        for tuning in (None, {"chunk": 32, "target_group": 32}, {"chunk": 256, "target_group": 128}):
+        for tuning in (None, {"chunk": 32, "target_group": 32, "warp_boxes": -1},
+                       {"chunk": 256, "target_group": 128, "warp_boxes": -1}, {"warp_boxes": 4}, {"warp_boxes": 1}):
             plan = _plan(api, wl, "helmholtz", layout, tuning=tuning)
             out = plan.apply(torch.from_numpy(lam).cuda()).cpu().numpy()
             assert rel_l2(out, ref).max() <= TOL
