@@ -875,6 +875,114 @@ def run_batched(args):
     return 0
 
 
+def _plate_points(n, seed):
+    """n points uniform on the square z = 0.5 of the unit cube: the paper's random points on a square plate."""
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(np.concatenate([rng.random((n, 2)), np.full((n, 1), 0.5)], axis=1).astype(np.float32))
+
+
+def run_tree_sweep(args):
+    """The layout comparison of the paper's Fig. 6 (Sec. 4.6) on GB300: square plates of N = 4^L points, the
+    CT = 15 tree level (4 points per box on average: N = 4 x boxes) raised or lowered by i in {-3 .. 3}, i.e. a
+    plate grid of 2^(L - 1 + i) boxes per side, D = 4 / 4^i points per box.  Laplace kernel (the paper applies a
+    potential kernel).  Per configuration: kernel-only time of the indexed layout (Sec. 3.2), the box-level
+    redundant layout, the paper's per-target repetition layout (Sec. 3.3) and the direct kernel, plus the
+    repetition layout's per-apply strength repack; the speedup of repetition over indexing, X = T_indexed /
+    T_repetition, next to the paper's kernel model (eq. 28), X = 55.3 lambda t / (N D), whose lambda is fitted
+    by least squares in log space over the measured points."""
+    import torch
+    from paper_2403_01596_gb300 import _capi as C, api, workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    path = C.P2P_PATH_FP32_SHARED
+    rows = []
+    Ls = [int(v) for v in args.tree_levels.split(",")]
+    for L in Ls:
+        n = 4 ** L
+        pts_np = _plate_points(n, 100 + L)
+        pts = torch.from_numpy(pts_np).cuda()
+        lam = torch.from_numpy(W.strengths(n, 1, 100 + L)).cuda()
+        out = torch.empty_like(lam)
+        for i in range(-3, 4):
+            lev = L - 1 + i
+            if lev < 0 or lev > 20:
+                continue
+            ng = 2 ** lev
+            st = api.BoxStructure(pts, (0.0, 0.0, 0.0), 1.0 / ng, ng)
+            sizes = torch.diff(st.box_ptr.long())
+            t_max = int(sizes.max().item())
+            D = n / st.num_boxes
+            row = {"L": L, "i": i, "N": n, "ng": ng, "boxes": st.num_boxes, "D": D, "t": t_max, "ms": {}}
+            for name, layout, tuning in (("indexed", "indexed", {"warp_boxes": -1}),
+                                          ("redundant", "redundant", {"warp_boxes": -1}),
+                                          ("repetition", "repetition", None),
+                                          ("direct", "indexed", {"warp_boxes": 4 if D <= 12 else 1}),
+                                          ("direct8", "indexed", {"warp_boxes": 8}),
+                                          ("direct16", "indexed", {"warp_boxes": 16}),
+                                          ("direct32", "indexed", {"warp_boxes": 32}),
+                                          ("auto", "indexed", None)):
+                try:
+                    plan = api.Plan(pts, (0.0, 0.0, 0.0), 1.0 / ng, ng, 0.0, kernel="laplace", layout=layout,
+                                    tuning=tuning, structure=st)
+                except C.P2PError as e:  # records beyond 2^31 entries: not measured
+                    row["ms"][name] = None
+                    row.setdefault("skipped", {})[name] = str(e)
+                    continue
+                if "pairs" not in row:
+                    row["pairs"] = plan.pair_count()
+                evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.ext_steps)]
+                for r in range(3 + args.ext_steps):
+                    e = evs[r - 3] if r >= 3 else None
+                    if e:
+                        e[0].record(stream)
+                    C.p2p_apply_stage(plan._plan, lam, 1, 1, path, stream)
+                    if e:
+                        e[1].record(stream)
+                    C.p2p_apply_staged(plan._plan, out, 1, 1, 0, path, stream)
+                    if e:
+                        e[2].record(stream)
+                torch.cuda.synchronize()
+                row["ms"][name] = statistics.median(e[1].elapsed_time(e[2]) for e in evs)
+                if name == "repetition":
+                    row["repack_ms"] = statistics.median(e[0].elapsed_time(e[1]) for e in evs)
+                    row["records"] = plan.records
+                plan.close()
+                del plan
+            ms = row["ms"]
+            if ms.get("repetition") and ms.get("indexed"):
+                row["X_rep_over_indexed"] = ms["indexed"] / ms["repetition"]
+            if ms.get("redundant") and ms.get("indexed"):
+                row["X_redundant_over_indexed"] = ms["indexed"] / ms["redundant"]
+            if ms.get("repetition") and ms.get("direct"):
+                row["X_rep_over_direct"] = ms["direct"] / ms["repetition"]
+            rows.append(row)
+            torch.cuda.empty_cache()
+    # fit of the paper's kernel model (eq. 28): X = 55.3 lambda t / (N D); log X = log lambda + log(55.3 t / (N D))
+    pts_fit = [(r["X_rep_over_indexed"], 55.3 * r["t"] / (r["N"] * r["D"])) for r in rows if "X_rep_over_indexed" in r]
+    fit = None
+    if pts_fit:
+        lx = np.log([p[0] for p in pts_fit])
+        lm = np.log([p[1] for p in pts_fit])
+        log_lam = float(np.mean(lx - lm))
+        pred = lm + log_lam
+        ss_res = float(np.sum((lx - pred) ** 2))
+        ss_tot = float(np.sum((lx - lx.mean()) ** 2))
+        fit = {"model": "X = 55.3 lambda t / (N D) (eq. 28)", "lambda_gpu": float(np.exp(log_lam)),
+               "r2_log": 1.0 - ss_res / ss_tot if ss_tot > 0 else None,
+               "corr_log": float(np.corrcoef(lx, lm)[0, 1]) if len(lx) > 2 else None,
+               "points": len(pts_fit), "paper_lambda_gpu": 640.0}
+        for r in rows:
+            if "X_rep_over_indexed" in r:
+                r["X_model"] = float(np.exp(log_lam) * 55.3 * r["t"] / (r["N"] * r["D"]))
+    line = {"metric": METRIC + " [layout comparison, Fig. 6 analogue]", "value": None, "unit": UNIT, "n_gpus": 1,
+            "steps": args.ext_steps, "warmup": 3, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "plate_tree_sweep", "levels": Ls, "i": list(range(-3, 4)), "CT": 15,
+                       "kernel": "laplace", "nrhs": 1, "l2": "not flushed (kernel-only times of small problems)"},
+            "rows": rows, "model_fit": fit}
+    print(json.dumps(line))
+    return 0
+
+
 def run_cube(args):
     """Dense uniform cube (32 768 points, 8^3 boxes, k = 8 pi), both source layouts: device-timed applies
     (L2 flushed between them) and the full FP64 oracle on every target."""
@@ -947,7 +1055,9 @@ def main():
                     help="direct kernel boxes per warp (1, 2, 4), -1 for the staged pipeline, 0: library default")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("sweep", "cube", "multirhs", "grad", "batched"), default="sweep",
+    ap.add_argument("--tree-levels", default="5,6,7,8,9,10", help="tree_sweep: plate sizes N = 4^L")
+    ap.add_argument("--workload", choices=("sweep", "cube", "multirhs", "grad", "batched", "tree_sweep"),
+                    default="sweep",
                     help="sweep (default): the occupancy sweep; the others measure the extension paths")
     ap.add_argument("--scale", type=float, default=1.0, help="point-count scale of the extension workloads")
     ap.add_argument("--ext-steps", type=int, default=20)
@@ -969,6 +1079,8 @@ def main():
         return run_grad(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "tree_sweep":
+        return run_tree_sweep(args)
     return run_ours(args)
 
 

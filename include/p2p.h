@@ -27,6 +27,16 @@
  *                         Same results, about half the kernel evaluations; results
  *                         are accumulated with atomics.  p2p_grad_points needs an
  *                         indexed or redundant plan.
+ *   P2P_LAYOUT_REPETITION the paper's own repetition layout (Sec. 3.3, eq. 8 - 9):
+ *                         every TARGET owns one contiguous record -- its coordinates,
+ *                         then a copy of every source of its box's neighbourhood --
+ *                         and one thread evaluates one target by reading its record
+ *                         front to back; the strengths are repacked into the records
+ *                         at every apply.  Records are not padded to 27 CT entries
+ *                         (each is 1 + S_b long, offsets kept per target).  One
+ *                         point set, max_nrhs 1; see p2p_repetition_records for the
+ *                         workspace.  Other calls on such a plan (batched launch,
+ *                         coordinate gradient) run on its indexed lists.
  *
  * Conventions shared by every entry point
  *   - Memory.  Pointers marked [dev] are CUDA device pointers, [host] are host
@@ -80,7 +90,12 @@ typedef enum {
 
 typedef enum { P2P_HELMHOLTZ = 0, P2P_LAPLACE = 1 } p2p_kernel;
 
-typedef enum { P2P_LAYOUT_INDEXED = 0, P2P_LAYOUT_REDUNDANT = 1, P2P_LAYOUT_SYMMETRIC = 2 } p2p_layout;
+typedef enum {
+    P2P_LAYOUT_INDEXED = 0,
+    P2P_LAYOUT_REDUNDANT = 1,
+    P2P_LAYOUT_SYMMETRIC = 2,
+    P2P_LAYOUT_REPETITION = 3
+} p2p_layout;
 
 /* Evaluation path of p2p_apply_path (the plain p2p_apply picks P2P_PATH_AUTO). */
 typedef enum {
@@ -100,18 +115,18 @@ typedef enum {
  *
  * warp_boxes selects the kernel of one-right-hand-side FP32 applies.  The staged
  * pipeline stages chunks of a box's source list in shared memory and suits boxes
- * of many targets; the direct kernel gives each warp 1, 2 or 4 whole boxes (32,
- * 16 or 8 lanes each) and reads the sources through the L1, which suits sparse
- * boxes (a few targets each), where a staged item carries too little work for
- * its fixed cost.  0: the plan decides from its mean box occupancy; -1: the
- * staged pipeline; 1, 2 or 4: the direct kernel with that many boxes per warp.
+ * of many targets; the direct kernel gives each warp 1, 2, 4, 8, 16 or 32 whole
+ * boxes (32 / warp_boxes lanes each) and reads the sources through the L1, which
+ * suits sparse boxes (a few targets each), where a staged item carries too little
+ * work for its fixed cost.  0: the plan decides from its mean box occupancy; -1:
+ * the staged pipeline; 1 .. 32: the direct kernel with that many boxes per warp.
  * Multi-RHS applies, the symmetric layout and the batched launch always use the
  * staged pipeline. */
 typedef struct {
     int32_t chunk;         /* sources staged per work item, multiple of 32, 32..1024 (default 192) */
     int32_t warps_per_cta; /* warps per thread block of the pair kernel, 1..16 (default 8) */
     int32_t target_group;  /* targets swept per pass, multiple of 32, 32..128 (default 32) */
-    int32_t warp_boxes;    /* 0 (plan decides), -1 (staged pipeline), 1, 2 or 4 (direct kernel) */
+    int32_t warp_boxes;    /* 0 (plan decides), -1 (staged pipeline), 1, 2, 4, 8, 16 or 32 (direct kernel) */
 } p2p_tuning;
 
 typedef struct p2p_plan p2p_plan;
@@ -270,6 +285,19 @@ P2P_API p2p_status p2p_build_neighbors_st(const int64_t* tgt_keys, int32_t num_t
 P2P_API p2p_status p2p_plan_workspace_size(int64_t n, int32_t num_boxes, int64_t nnz, int64_t sources,
                                            p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
                                            size_t* bytes);
+
+/*
+ * Size of the per-target records of P2P_LAYOUT_REPETITION: records = sum over
+ * boxes b of n_b (1 + S_b) entries (the paper's memory estimate, eq. 8, without
+ * its padding), computed from the box pointers and neighbour lists of
+ * p2p_bin_points / p2p_build_neighbors (copied to the host; synchronises).
+ * p2p_plan_workspace_size_rep gives the workspace of such a plan; records must
+ * stay below 2^31.
+ */
+P2P_API p2p_status p2p_repetition_records(const int32_t* box_ptr, int32_t num_boxes, const int32_t* nbr_ptr,
+                                          const int32_t* nbr_idx, int64_t* records, p2p_stream_t stream);
+P2P_API p2p_status p2p_plan_workspace_size_rep(int64_t n, int32_t num_boxes, int64_t nnz, int64_t sources,
+                                               int64_t records, const p2p_tuning* tuning, size_t* bytes);
 P2P_API p2p_status p2p_plan_create(p2p_plan** plan, const float* pts, int64_t n, const int32_t* perm,
                                    const int32_t* box_ptr, int32_t num_boxes, const int32_t* nbr_ptr,
                                    const int32_t* nbr_idx, int64_t nnz, int64_t sources, p2p_kernel kernel,
@@ -389,6 +417,34 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
  */
 P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, const void* g, float* grad,
                                    int32_t nrhs, int64_t ld, p2p_stream_t stream);
+
+/*
+ * Guarded apply: p2p_apply_path with every result within a relative tolerance
+ * of the exact sum (the north-star's FP64 final reduction "when the relative
+ * error exceeds 1e-6", made per target).  An evaluation whose terms G lambda are
+ * each accurate to a relative delta has |out_i - exact_i| <= delta S_i with
+ * S_i = sum_j |G(r_ij) lambda_j|; the call computes S (a Laplace sweep over
+ * |lambda|), flags every target with delta S_i > tol |out_i| for some right-hand
+ * side (the sums that cancel: S_i / |out_i| large), and re-evaluates the flagged
+ * targets in FP64 on the GPU (their whole neighbourhood, every right-hand side),
+ * overwriting their FP32 results.  delta: 2^-20 for the FP32 paths, 2^-14 for
+ * the tensor-core path; path AUTO takes the tensor-core path only when
+ * 32 * 2^-14 <= tol.  For strengths with random phases most targets have
+ * S_i / |out_i| of 10 - 30, so tol = 1e-6 re-evaluates most of them; tol = 1e-4
+ * picks out the strongly cancelling ones.
+ *
+ *   tol          relative tolerance per target and right-hand side, >= 0
+ *   work   [dev] at least p2p_apply_guarded_workspace_size bytes, 256-byte aligned
+ *   refined [host] out (may be NULL): targets re-evaluated in FP64
+ *
+ * Other arguments as for p2p_apply_path.  Not for symmetric-layout plans
+ * (P2P_ERR_UNSUPPORTED).  Synchronises once (to read the number of flagged
+ * targets).
+ */
+P2P_API p2p_status p2p_apply_guarded_workspace_size(const p2p_plan* plan, int32_t nrhs, size_t* bytes);
+P2P_API p2p_status p2p_apply_guarded(const p2p_plan* plan, const void* lambda, void* out, int32_t nrhs, int64_t ld,
+                                     int32_t adjoint, p2p_path path, double tol, void* work, size_t work_bytes,
+                                     int64_t* refined, p2p_stream_t stream);
 
 /* ----------------------------------------------------- batched apply --- */
 /*

@@ -27,6 +27,7 @@ P2P_LAPLACE = 1
 P2P_LAYOUT_INDEXED = 0
 P2P_LAYOUT_REDUNDANT = 1
 P2P_LAYOUT_SYMMETRIC = 2
+P2P_LAYOUT_REPETITION = 3
 P2P_PATH_AUTO = 0
 P2P_PATH_FP32_PER_RHS = 1
 P2P_PATH_FP32_SHARED = 2
@@ -78,6 +79,10 @@ def load(build_if_missing: bool = True):
             "p2p_bin_points_static": ([P, i64, P, dbl, i32, P, P, P, P, PI32, P], ctypes.c_int),
             "p2p_neighbors_workspace_size": ([i32, PSZ], ctypes.c_int),
             "p2p_build_neighbors": ([P, P, i32, i32, P, P, PI64, PI64, P, sz, P], ctypes.c_int),
+            "p2p_apply_guarded_workspace_size": ([P, i32, PSZ], ctypes.c_int),
+            "p2p_apply_guarded": ([P, P, P, i32, i64, i32, ctypes.c_int, dbl, P, sz, PI64, P], ctypes.c_int),
+            "p2p_repetition_records": ([P, i32, P, P, PI64, P], ctypes.c_int),
+            "p2p_plan_workspace_size_rep": ([i64, i32, i64, i64, i64, P, PSZ], ctypes.c_int),
             "p2p_plan_update_points": ([P, P, P, dbl, i32, PI64, P], ctypes.c_int),
             "p2p_build_neighbors_st": ([P, i32, P, P, i32, i32, P, P, P, PI64, PI64, P, sz, P], ctypes.c_int),
             "p2p_plan_workspace_size": ([i64, i32, i64, i64, ctypes.c_int, i32, P, PSZ], ctypes.c_int),
@@ -256,6 +261,20 @@ def p2p_plan_info(plan) -> dict:
                                                "target_group": t.target_group, "warp_boxes": t.warp_boxes}}
 
 
+def p2p_repetition_records(box_ptr, num_boxes, nbr_ptr, nbr_idx, stream=None) -> int:
+    out = ctypes.c_int64(0)
+    check(load().p2p_repetition_records(_ptr(box_ptr), int(num_boxes), _ptr(nbr_ptr), _ptr(nbr_idx),
+                                        ctypes.byref(out), _stream(stream)), "p2p_repetition_records")
+    return out.value
+
+
+def p2p_plan_workspace_size_rep(n, num_boxes, nnz, sources, records, tuning=None) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().p2p_plan_workspace_size_rep(n, num_boxes, nnz, sources, records, _tuning(tuning),
+                                             ctypes.byref(out)), "p2p_plan_workspace_size_rep")
+    return out.value
+
+
 def p2p_plan_update_points(plan, pts, lo, h, ng, stream=None):
     """New coordinates for a plan; returns (status, moved): P2P_OK, or P2P_ERR_STALE when `moved` points would
     change leaf box (the plan is then unchanged).  Other failures raise."""
@@ -386,3 +405,18 @@ def p2p_host_pipe_destroy(pipe):
 
 def p2p_diag_tc_wait_limit(plan, polls: int):
     check(load().p2p_diag_tc_wait_limit(plan, int(polls)), "p2p_diag_tc_wait_limit")
+
+
+def p2p_apply_guarded_workspace_size(plan, nrhs) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().p2p_apply_guarded_workspace_size(plan, int(nrhs), ctypes.byref(out)),
+          "p2p_apply_guarded_workspace_size")
+    return out.value
+
+
+def p2p_apply_guarded(plan, lam, out, nrhs, ld, adjoint, path, tol, work, stream=None) -> int:
+    refined = ctypes.c_int64(0)
+    check(load().p2p_apply_guarded(plan, _ptr(lam), _ptr(out), int(nrhs), int(ld), int(adjoint), int(path),
+                                   float(tol), _ptr(work), work.numel(), ctypes.byref(refined), _stream(stream)),
+          "p2p_apply_guarded")
+    return refined.value

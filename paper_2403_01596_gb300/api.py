@@ -20,7 +20,7 @@ from . import _capi as C
 
 KERNELS = {"helmholtz": C.P2P_HELMHOLTZ, "laplace": C.P2P_LAPLACE}
 LAYOUTS = {"indexed": C.P2P_LAYOUT_INDEXED, "redundant": C.P2P_LAYOUT_REDUNDANT,
-           "symmetric": C.P2P_LAYOUT_SYMMETRIC}
+           "symmetric": C.P2P_LAYOUT_SYMMETRIC, "repetition": C.P2P_LAYOUT_REPETITION}
 PATHS = {"auto": C.P2P_PATH_AUTO, "fp32_per_rhs": C.P2P_PATH_FP32_PER_RHS, "fp32_shared": C.P2P_PATH_FP32_SHARED,
          "tc_bf16x3": C.P2P_PATH_TC_BF16X3}
 
@@ -94,8 +94,13 @@ class Plan:
         st = self.structure
         kernel, layout, tuning = self.kernel, self.layout, self.tuning
         dev = st.points.device
-        ws = C.p2p_plan_workspace_size(st.n, st.num_boxes, st.nnz, st.sources, LAYOUTS[layout], self.max_nrhs,
-                                       tuning)
+        if layout == "repetition":
+            # the paper's per-target records: sum over boxes of n_b (1 + S_b) entries
+            self.records = C.p2p_repetition_records(st.box_ptr, st.num_boxes, st.nbr_ptr, st.nbr_idx, _stream())
+            ws = C.p2p_plan_workspace_size_rep(st.n, st.num_boxes, st.nnz, st.sources, self.records, tuning)
+        else:
+            ws = C.p2p_plan_workspace_size(st.n, st.num_boxes, st.nnz, st.sources, LAYOUTS[layout], self.max_nrhs,
+                                           tuning)
         self.workspace = _bytes(ws, dev)
         self._plan = C.p2p_plan_create(st.points, st.perm, st.box_ptr, st.num_boxes, st.nbr_ptr, st.nbr_idx, st.nnz,
                                        st.sources, KERNELS[kernel], self.k, LAYOUTS[layout], self.max_nrhs, tuning,
@@ -178,6 +183,20 @@ class Plan:
             out = torch.empty_like(lam2)
         C.p2p_apply_path(self._plan, lam2, out, nrhs, nrhs, int(adjoint), PATHS[path], _stream())
         return out.reshape(lam.shape)
+
+    def apply_guarded(self, lam: torch.Tensor, tol: float = 1e-6, adjoint: bool = False, path: str = "auto",
+                      out: torch.Tensor | None = None):
+        """apply() with every result within relative `tol` of the exact sum: targets whose FP32 error bound
+        (2^-20 sum_j |G lambda_j|) exceeds tol |out| are re-evaluated in FP64 on the GPU.  Returns (out, number
+        of targets re-evaluated)."""
+        lam2 = self._check_lam(lam).contiguous()
+        nrhs = lam2.shape[1]
+        if out is None:
+            out = torch.empty((self.n, nrhs), dtype=torch.complex64, device=lam.device)
+        work = _bytes(C.p2p_apply_guarded_workspace_size(self._plan, nrhs), lam.device)
+        refined = C.p2p_apply_guarded(self._plan, lam2, out, nrhs, nrhs, int(adjoint), PATHS[path], tol, work,
+                                      _stream())
+        return (out.reshape(self.n) if lam.dim() == 1 else out), refined
 
     def grad_points(self, lam: torch.Tensor, g: torch.Tensor) -> torch.Tensor:
         lam2 = self._check_lam(lam).contiguous()

@@ -31,6 +31,9 @@ DEFAULT_CANDIDATES = (
     {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 1},
     {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 2},
     {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 4},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 8},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 16},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 32},
 )
 
 DEFAULT_LAYOUTS = ("indexed", "redundant", "symmetric")

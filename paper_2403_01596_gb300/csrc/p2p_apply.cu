@@ -47,9 +47,37 @@ __global__ void __launch_bounds__(kDirectWarps * 32, P2P_DIRECT_MIN_BLOCKS)
 
 using DirectKernel = void (*)(DirectArgs);
 
+// Repetition layout (Sec. 3.3, eq. 9): one thread per target, reading its own record front to back -- entry 0
+// its coordinates, entries 1 .. S_b its neighbourhood's sources with the strengths repacked at this apply.  The
+// record holds the target itself among its own box's sources: the r = 0 mask applies to every entry.
+template <int KERN>
+__global__ void __launch_bounds__(256) k_pair_rep(const int32_t* __restrict__ rec_off,
+                                                  const float4* __restrict__ rec_xyz,
+                                                  const float2* __restrict__ rec_lam, const int32_t* __restrict__ perm,
+                                                  int64_t n, float k, float2* __restrict__ out, int64_t ld) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int32_t off = rec_off[t], end = rec_off[t + 1];
+    const float4 x = rec_xyz[off];
+    const float4 tx[1] = {x};
+    float2 acc[1][1] = {{make_float2(0.f, 0.f)}};
+    for (int32_t e = off + 1; e < end; ++e) {
+        const float2 l[1] = {rec_lam[e]};
+        pair_core<KERN, 1, 1, true>(rec_xyz[e], l, tx, acc, k);
+    }
+    out[(int64_t)perm[t] * ld] = make_float2(acc[0][0].x * kInv4Pi, acc[0][0].y * kInv4Pi);
+}
+
 template <int KERN, bool RED>
 DirectKernel direct_kernel_k(int k) {
-    return k == 1 ? k_pair_direct<KERN, RED, 1> : (k == 2 ? k_pair_direct<KERN, RED, 2> : k_pair_direct<KERN, RED, 4>);
+    switch (k) {
+        case 1: return k_pair_direct<KERN, RED, 1>;
+        case 2: return k_pair_direct<KERN, RED, 2>;
+        case 4: return k_pair_direct<KERN, RED, 4>;
+        case 8: return k_pair_direct<KERN, RED, 8>;
+        case 16: return k_pair_direct<KERN, RED, 16>;
+        default: return k_pair_direct<KERN, RED, 32>;
+    }
 }
 
 DirectKernel direct_kernel(const p2p_plan* p) {
@@ -282,6 +310,23 @@ cudaError_t stage_rows(const float2* src, int64_t ld, const int32_t* rows, int64
     return cudaGetLastError();
 }
 
+// dst[s * nrhs + q] = (|src[rows[s] * ld + q]|, 0)  (rows[s] < 0: zero): the strengths' magnitudes, for the sums
+// of the terms' magnitudes of a guarded apply.
+__global__ void k_gather_abs(const float2* __restrict__ src, int64_t ld, const int32_t* __restrict__ rows, int64_t n,
+                             int32_t nrhs, float2* __restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nrhs) return;
+    const int64_t s = i / nrhs;
+    const int q = (int)(i - s * nrhs);
+    const int32_t r = rows[s];
+    float m = 0.f;
+    if (r >= 0) {
+        const float2 v = src[(int64_t)r * ld + q];
+        m = hypotf(v.x, v.y);
+    }
+    dst[i] = make_float2(m, 0.f);
+}
+
 int r_index(int R) { return R == 1 ? 0 : (R == 2 ? 1 : 2); }
 
 // The dynamic shared-memory limit is an attribute of the kernel function,
@@ -362,6 +407,31 @@ p2p_status check_apply_args(const p2p_plan* plan, const void* lam, const void* o
 
 }  // namespace
 
+// S[perm[t] * nrhs + q] = sum over the sources s of target t's neighbourhood (r > 0) of |lambda_sq| / (4 pi r),
+// i.e. sum_s |G(r) lambda_sq| for both kernels (|exp(ikr)| = 1), through the staged pipeline with the Laplace
+// kernel on the strengths' magnitudes (lambda: leading dimension ld; S: nrhs).  Uses the plan's staging buffer.
+p2p_status p2p_abs_sums(const p2p_plan* plan, const float2* lam, int64_t ld, int32_t nrhs, float2* S, cudaStream_t s) {
+    const bool red = plan->layout == P2P_LAYOUT_REDUNDANT;
+    const int32_t* rows = red ? plan->pk_src : plan->src_perm;
+    const int64_t nrows = red ? plan->packed : plan->n_src;
+    if (nrows > 0) {
+        const int64_t total = nrows * nrhs;
+        k_gather_abs<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(lam, ld, rows, nrows, nrhs, plan->lam_buf);
+        P2P_CHECK_LAUNCH("p2p_apply_guarded/abs");
+    }
+    P2P_TRY_CUDA(cudaMemsetAsync(S, 0, (size_t)plan->n * nrhs * 8, s), "p2p_apply_guarded");
+    if (plan->n_items == 0 || nrows == 0) return P2P_OK;
+    PairArgs a = base_args(plan);
+    a.out = S;
+    a.ld = nrhs;
+    a.nrhs = nrhs;
+    a.kernel = P2P_LAPLACE;
+    a.k = 0.f;
+    a.atomic_out = 1;  // the buffer is zeroed above
+    const int R = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
+    return R == 1 ? launch_pair<1>(plan, a, s) : (R == 2 ? launch_pair<2>(plan, a, s) : launch_pair<4>(plan, a, s));
+}
+
 cudaError_t p2p_pair_configure(p2p_plan* plan) {
     cudaError_t e = configure_r<1>(plan);
     if (e == cudaSuccess) e = configure_r<2>(plan);
@@ -403,6 +473,12 @@ P2P_API p2p_status p2p_apply_stage(const p2p_plan* plan, const void* lambda, int
     if (path == P2P_PATH_TC_BF16X3 && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if (path == P2P_PATH_TC_BF16X3) return p2p_tc_stage(plan, (const float2*)lambda, nrhs, ld, s);
+    if (plan->layout == P2P_LAYOUT_REPETITION) {
+        // every target's record gets its own copy of its sources' strengths (the record head: 0)
+        P2P_TRY_CUDA(stage_rows((const float2*)lambda, ld, plan->rec_src, plan->records, 1, plan->lam_buf, s),
+                     "p2p_apply_stage");
+        return P2P_OK;
+    }
     const bool red = plan->layout == P2P_LAYOUT_REDUNDANT;
     const int32_t* rows = red ? plan->pk_src : plan->src_perm;  // strengths live on the sources
     const int64_t nrows = red ? plan->packed : plan->n_src;
@@ -425,6 +501,18 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
         P2P_TRY_CUDA(cudaMemset2DAsync(out, (size_t)ld * 8, 0, (size_t)nrhs * 8, (size_t)plan->n, s), "p2p_apply/zero");
     if (plan->n_src == 0) return P2P_OK;
     if (path == P2P_PATH_TC_BF16X3) return p2p_apply_tc(plan, (float2*)out, nrhs, ld, adjoint, s);
+    if (plan->layout == P2P_LAYOUT_REPETITION) {
+        const float k = adjoint ? -plan->k : plan->k;
+        const unsigned blocks = (unsigned)((plan->n + 255) / 256);
+        if (plan->kernel == P2P_HELMHOLTZ)
+            k_pair_rep<P2P_HELMHOLTZ><<<blocks, 256, 0, s>>>(plan->rec_off, plan->rec_xyz, plan->lam_buf, plan->perm,
+                                                              plan->n, k, (float2*)out, ld);
+        else
+            k_pair_rep<P2P_LAPLACE><<<blocks, 256, 0, s>>>(plan->rec_off, plan->rec_xyz, plan->lam_buf, plan->perm,
+                                                            plan->n, k, (float2*)out, ld);
+        P2P_CHECK_LAUNCH("p2p_apply/repetition");
+        return P2P_OK;
+    }
     PairArgs a = base_args(plan);
     a.out = (float2*)out;
     a.ld = ld;

@@ -5,7 +5,8 @@
 // amount of work per item -- record, bulk / cp.async staging, waits, slice
 // reduction -- that a box of ~8 targets against ~100 sources cannot amortise:
 // each lane then sweeps only a dozen sources.  Here a warp serves K boxes at
-// once (K = 1, 2 or 4; 32 / K lanes per box), an item is one whole box (its
+// once (K = 1, 2, 4, 8, 16 or 32; 32 / K lanes per box, down to one lane per box
+// for boxes of a point or two), an item is one whole box (its
 // complete source list, so every result is written once, without atomics), and
 // the sources are read straight from global memory through the L1, with the
 // next sources prefetched into registers, instead of being staged in shared

@@ -97,6 +97,12 @@ struct p2p_plan {
     int32_t* nb_src;        // [packed] box-sorted index of every listed source, -1 for padding
     float4* pk_xyz;         // [packed] redundant layout: per-box copy of the listed coordinates
     int32_t* pk_src;        // [packed] redundant layout: original index of every listed source, -1 for padding
+    // repetition layout (Sec. 3.3): one record per target -- its coordinates, then its neighbourhood's sources
+    int64_t records;        // entries of all records (sum over boxes of n_b (1 + S_b)), 0 for other layouts
+    int32_t* rec_off;       // [n + 1] first entry of the record of every target (box-sorted order)
+    float4* rec_xyz;        // [records] coordinates: the target, then its sources
+    int32_t* rec_src;       // [records] original index of every source entry, -1 for the target entry
+    int32_t* rec_boff;      // [nb + 1] first record entry of every box
     int32_t direct_k;       // boxes per warp of the direct kernel (1, 2 or 4); 0: the staged pipeline
     ItemRec* ditems;        // [nb] direct kernel: one item per target box (whole source list, lane maps for
                             // 32 / direct_k lanes), heaviest first

@@ -457,6 +457,42 @@ __global__ void k_repack_xyz(const float4* __restrict__ xs, const int32_t* __res
     pk_xyz[p] = j >= 0 ? xs[j] : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Repetition layout: entries of the records of box b's targets, n_b (1 + S_b).
+__global__ void k_rep_count(const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ box_src, int32_t nb,
+                            int32_t* __restrict__ cnt) {
+    const int32_t b = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (b < nb) cnt[b] = (box_ptr[b + 1] - box_ptr[b]) * (1 + box_src[b]);
+}
+
+// One warp per box: the records of its targets -- entry 0 the target's coordinates, entries 1 .. S_b a copy of
+// the box's source list (own box first, then the other neighbour boxes in ascending id) with the sources'
+// original indices, for the per-apply strength repack (the collection of Sec. 3.3, eq. 6, on the device).
+__global__ void k_rep_fill(const float4* __restrict__ xs, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ box_ptr, const int32_t* __restrict__ box_src,
+                           const int32_t* __restrict__ pk_off, const int32_t* __restrict__ nb_src,
+                           const int32_t* __restrict__ rec_boff, int32_t nb, int64_t n, int32_t* __restrict__ rec_off,
+                           float4* __restrict__ rec_xyz, int32_t* __restrict__ rec_src) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const int32_t tb = box_ptr[b], nt = box_ptr[b + 1] - tb, S = box_src[b], len = 1 + S;
+    const int32_t* list = nb_src + pk_off[b];
+    for (int32_t u = 0; u < nt; ++u) {
+        const int64_t base = (int64_t)rec_boff[b] + (int64_t)u * len;
+        if (lane == 0) {
+            rec_off[tb + u] = (int32_t)base;
+            rec_xyz[base] = xs[tb + u];
+            rec_src[base] = -1;
+        }
+        for (int32_t p = lane; p < S; p += 32) {
+            const int32_t j = list[p];
+            rec_xyz[base + 1 + p] = xs[j];
+            rec_src[base + 1 + p] = perm[j];
+        }
+    }
+    if (b == nb - 1 && lane == 0) rec_off[n] = rec_boff[nb];
+}
+
 int ceil_log2(int v) {
     int b = 0;
     while ((1 << b) < v) ++b;
@@ -510,7 +546,8 @@ NbrLayout nbr_layout(int32_t nb, void* work) {
 bool tuning_valid(const p2p_tuning& t) {
     return t.chunk >= 32 && t.chunk <= 1024 && t.chunk % 32 == 0 && t.warps_per_cta >= 1 && t.warps_per_cta <= 16 &&
            t.target_group >= 32 && t.target_group <= 128 && t.target_group % 32 == 0 &&
-           (t.warp_boxes == -1 || t.warp_boxes == 0 || t.warp_boxes == 1 || t.warp_boxes == 2 || t.warp_boxes == 4);
+           (t.warp_boxes == -1 || t.warp_boxes == 0 || t.warp_boxes == 1 || t.warp_boxes == 2 || t.warp_boxes == 4 ||
+            t.warp_boxes == 8 || t.warp_boxes == 16 || t.warp_boxes == 32);
 }
 
 // Default launch tuning; a plan whose caller leaves chunk and warps at zero may switch to kWideTuning (see
@@ -531,13 +568,19 @@ p2p_tuning resolve_tuning(const p2p_tuning* t) {
     return r;
 }
 
-// Boxes per warp of the direct kernel for a plan left to choose (warp_boxes = 0): four boxes per warp when
-// the mean box holds at most 12 targets (measured on the 2^20-point sphere: 187 us against 217 us for the
-// staged pipeline at 8 points per box), the staged pipeline above that (16 points per box: 290 us staged,
-// 293 - 340 us direct).
+// Boxes per warp of the direct kernel for a plan left to choose (warp_boxes = 0), from the mean number of
+// targets per box D.  Measured on GB300: the 2^20-point sphere at D = 8 (185 us with four boxes per warp
+// against 217 us staged) and D = 16 (staged 290 us, direct 293 - 340 us), and square plates of 2^10 - 2^20
+// points at D = 1.0 - 4 (at 2^20 points: D = 4.1, eight boxes per warp 74 us, four 82 us, staged 258 us;
+// D = 1.6, sixteen 64 us; D = 1.0 - 1.1, thirty-two 39 - 47 us).
 int32_t auto_warp_boxes(int64_t n, int32_t nb) {
     if (nb <= 0) return -1;
-    return (double)n / nb <= 12.0 ? 4 : -1;
+    const double d = (double)n / nb;
+    if (d <= 1.3) return 32;
+    if (d <= 2.5) return 16;
+    if (d <= 6.0) return 8;
+    if (d <= 12.0) return 4;
+    return -1;
 }
 
 struct PlanLayout {
@@ -554,7 +597,7 @@ struct PlanLayout {
 
 // Sizes of a plan: n targets in nb boxes, n_src sources in nbs boxes (two_sets), sources = sum of S_b.
 PlanLayout plan_layout(int64_t n, int32_t nb, int64_t n_src, int32_t nbs, bool two_sets, int64_t sources, int64_t nnz,
-                       p2p_layout layout, int32_t max_nrhs, const p2p_tuning& t, void* ws) {
+                       p2p_layout layout, int32_t max_nrhs, const p2p_tuning& t, void* ws, int64_t records = 0) {
     Carver c{static_cast<char*>(ws), 0, (size_t)-1};
     PlanLayout L;
     memset(&L.p, 0, sizeof(L.p));
@@ -574,7 +617,14 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t n_src, int32_t nbs, bool t
     L.p.nb_src = c.take<int32_t>(list_bound);
     L.p.pk_xyz = red ? c.take<float4>(list_bound) : nullptr;
     L.p.pk_src = red ? c.take<int32_t>(list_bound) : nullptr;
-    const size_t lam_rows = red ? (ms > list_bound ? ms : list_bound) : ms;
+    const bool rep = layout == P2P_LAYOUT_REPETITION;
+    const size_t mr = (size_t)(records > 0 ? records : 1);
+    L.p.rec_off = rep ? c.take<int32_t>(m + 1) : nullptr;
+    L.p.rec_boff = rep ? c.take<int32_t>(mb + 1) : nullptr;
+    L.p.rec_xyz = rep ? c.take<float4>(mr) : nullptr;
+    L.p.rec_src = rep ? c.take<int32_t>(mr) : nullptr;
+    size_t lam_rows = red ? (ms > list_bound ? ms : list_bound) : ms;
+    if (rep && mr > lam_rows) lam_rows = mr;
     const size_t lam_bytes = lam_rows * (size_t)max_nrhs * sizeof(float2);
     L.p.lam_buf = c.take<float2>(lam_rows * (size_t)max_nrhs);
     L.p.g_buf = two_sets ? nullptr : c.take<float2>(m * (size_t)max_nrhs);
@@ -640,9 +690,11 @@ p2p_status check_sizes(int64_t n, int32_t nb, int64_t n_src, int32_t nbs, int64_
     if (n < 0 || n >= INT32_MAX || nb < 0 || nb > n || n_src < 0 || n_src >= INT32_MAX || nbs < 0 || nbs > n_src ||
         sources < 0 || sources >= INT32_MAX || max_nrhs < 1 || max_nrhs > 256)
         return P2P_ERR_INVALID;
-    if (layout != P2P_LAYOUT_INDEXED && layout != P2P_LAYOUT_REDUNDANT && layout != P2P_LAYOUT_SYMMETRIC)
+    if (layout != P2P_LAYOUT_INDEXED && layout != P2P_LAYOUT_REDUNDANT && layout != P2P_LAYOUT_SYMMETRIC &&
+        layout != P2P_LAYOUT_REPETITION)
         return P2P_ERR_INVALID;
-    if (two_sets && layout == P2P_LAYOUT_SYMMETRIC) return P2P_ERR_UNSUPPORTED;
+    if (two_sets && (layout == P2P_LAYOUT_SYMMETRIC || layout == P2P_LAYOUT_REPETITION)) return P2P_ERR_UNSUPPORTED;
+    if (layout == P2P_LAYOUT_REPETITION && max_nrhs != 1) return P2P_ERR_UNSUPPORTED;
     return P2P_OK;
 }
 
@@ -788,6 +840,61 @@ p2p_status build_neighbors(const int64_t* box_keys, int32_t num_boxes, const int
     return P2P_OK;
 }
 
+// Entries of the repetition layout's records, sum over boxes of n_b (1 + S_b), from the box pointers and the
+// neighbour lists copied to the host.
+p2p_status repetition_records(const int32_t* box_ptr, int32_t nb, const int32_t* nbr_ptr, const int32_t* nbr_idx,
+                              int64_t* records, cudaStream_t s) {
+    *records = 0;
+    if (nb <= 0) return P2P_OK;
+    int32_t* hb = (int32_t*)malloc(sizeof(int32_t) * ((size_t)nb + 1) * 2);
+    if (!hb) return P2P_ERR_ALLOC;
+    int32_t* hp = hb + nb + 1;
+    cudaError_t e = cudaMemcpyAsync(hb, box_ptr, sizeof(int32_t) * ((size_t)nb + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hp, nbr_ptr, sizeof(int32_t) * ((size_t)nb + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int32_t* hi = nullptr;
+    const int64_t nnz = e == cudaSuccess ? hp[nb] : 0;
+    if (e == cudaSuccess && (nnz < 0 || nnz > 27ll * nb || hp[0] != 0)) {
+        free(hb);
+        return P2P_ERR_INVALID;
+    }
+    if (e == cudaSuccess && nnz > 0) {
+        hi = (int32_t*)malloc(sizeof(int32_t) * (size_t)nnz);
+        if (!hi) {
+            free(hb);
+            return P2P_ERR_ALLOC;
+        }
+        e = cudaMemcpyAsync(hi, nbr_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        free(hb);
+        free(hi);
+        set_cuda_error(e, "p2p_repetition_records");
+        return P2P_ERR_CUDA;
+    }
+    int64_t total = 0;
+    p2p_status st = P2P_OK;
+    for (int32_t b = 0; b < nb && st == P2P_OK; ++b) {
+        int64_t sb = 0;
+        for (int32_t q = hp[b]; q < hp[b + 1]; ++q) {
+            const int32_t c = hi[q];
+            if (c < 0 || c >= nb) {
+                st = P2P_ERR_INVALID;
+                break;
+            }
+            sb += hb[c + 1] - hb[c];
+        }
+        total += (int64_t)(hb[b + 1] - hb[b]) * (1 + sb);
+    }
+    free(hb);
+    free(hi);
+    if (st != P2P_OK) return st;
+    *records = total;
+    return P2P_OK;
+}
+
 p2p_status plan_create(p2p_plan** plan, const PlanInput& in, p2p_kernel kernel, float k, p2p_layout layout,
                        int32_t max_nrhs, const p2p_tuning* tuning, void* workspace, size_t workspace_bytes,
                        cudaStream_t s) {
@@ -811,8 +918,14 @@ p2p_status plan_create(p2p_plan** plan, const PlanInput& in, p2p_kernel kernel, 
         return P2P_ERR_INVALID;
     if (!workspace || ((uintptr_t)workspace & 255) || ((uintptr_t)in.pts & 3) || ((uintptr_t)in.src_pts & 3))
         return P2P_ERR_INVALID;
+    int64_t records = 0;
+    if (layout == P2P_LAYOUT_REPETITION) {
+        const p2p_status rs = repetition_records(in.box_ptr, nb, in.nbr_ptr, in.nbr_idx, &records, s);
+        if (rs != P2P_OK) return rs;
+        if (records >= INT32_MAX) return P2P_ERR_UNSUPPORTED;
+    }
     PlanLayout L = plan_layout(n, nb, in.n_src, in.nbs, in.two_sets, in.sources, in.nnz, layout, max_nrhs, t,
-                               workspace);
+                               workspace, records);
     if (workspace_bytes < L.bytes) return P2P_ERR_WORKSPACE;
     p2p_plan* p = (p2p_plan*)malloc(sizeof(p2p_plan));
     if (!p) return P2P_ERR_ALLOC;
@@ -843,6 +956,7 @@ p2p_status plan_create(p2p_plan** plan, const PlanInput& in, p2p_kernel kernel, 
     p->max_box = 0;
     p->packed = 0;
     p->tc_wait_polls = -1;
+    p->records = records;
 #define FAIL_CUDA(expr, where)                 \
     do {                                       \
         cudaError_t e_ = (expr);               \
@@ -897,6 +1011,17 @@ p2p_status plan_create(p2p_plan** plan, const PlanInput& in, p2p_kernel kernel, 
                                                                       in.nbr_ptr, in.nbr_idx, p->nbr_self, p->pk_off,
                                                                       nb, upper, p->nb_src, p->pk_xyz, p->pk_src);
     FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/pack");
+    if (layout == P2P_LAYOUT_REPETITION) {
+        // per-target records (L.padded is free once the list offsets are scanned)
+        k_rep_count<<<blocks_for(nb, kThreads), kThreads, 0, s>>>(in.box_ptr, p->box_src, nb, L.padded);
+        FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/rep_count");
+        FAIL_CUDA(scan_exclusive_i32(L.padded, p->rec_boff, nb, p->rec_boff + nb, L.scan_ws, s),
+                  "p2p_plan_create/rep_scan");
+        k_rep_fill<<<blocks_for((int64_t)nb * 32, kThreads), kThreads, 0, s>>>(
+            p->xs, in.perm, in.box_ptr, p->box_src, p->pk_off, p->nb_src, p->rec_boff, nb, n, p->rec_off, p->rec_xyz,
+            p->rec_src);
+        FAIL_CUDA(cudaGetLastError(), "p2p_plan_create/rep_fill");
+    }
     k_item_records<<<blocks_for(nb, kThreads), kThreads, 0, s>>>(L.n_chunks, L.item_off, in.box_ptr, L.list_len,
                                                                  L.self_len, p->pk_off, nb, t.chunk, t.target_group,
                                                                  p->two_sets, L.recs, L.keys, L.vals);
@@ -948,7 +1073,7 @@ p2p_status plan_create(p2p_plan** plan, const PlanInput& in, p2p_kernel kernel, 
     }
     // direct kernel: one item per target box (the item-sort scratch is free again)
     p->direct_k = 0;
-    if (layout != P2P_LAYOUT_SYMMETRIC) {
+    if (layout != P2P_LAYOUT_SYMMETRIC && layout != P2P_LAYOUT_REPETITION) {
         const int32_t wb = t.warp_boxes == 0 ? auto_warp_boxes(n, nb) : t.warp_boxes;
         p->tune.warp_boxes = wb;
         if (wb > 0) {
@@ -1014,11 +1139,30 @@ P2P_API p2p_status p2p_plan_workspace_size(int64_t n, int32_t num_boxes, int64_t
                                            p2p_layout layout, int32_t max_nrhs, const p2p_tuning* tuning,
                                            size_t* bytes) {
     if (!bytes) return P2P_ERR_INVALID;
+    if (layout == P2P_LAYOUT_REPETITION) return P2P_ERR_INVALID;  // its records: p2p_plan_workspace_size_rep
     p2p_status st = check_sizes(n, num_boxes, n, num_boxes, sources, layout, max_nrhs, false);
     if (st != P2P_OK) return st;
     p2p_tuning t = resolve_tuning(tuning);
     if (!tuning_valid(t)) return P2P_ERR_INVALID;
     *bytes = plan_layout(n, num_boxes, n, num_boxes, false, sources, nnz, layout, max_nrhs, t, nullptr).bytes;
+    return P2P_OK;
+}
+
+P2P_API p2p_status p2p_repetition_records(const int32_t* box_ptr, int32_t num_boxes, const int32_t* nbr_ptr,
+                                          const int32_t* nbr_idx, int64_t* records, p2p_stream_t stream) {
+    if (!records || num_boxes < 0 || (num_boxes > 0 && (!box_ptr || !nbr_ptr || !nbr_idx))) return P2P_ERR_INVALID;
+    return repetition_records(box_ptr, num_boxes, nbr_ptr, nbr_idx, records, (cudaStream_t)stream);
+}
+
+P2P_API p2p_status p2p_plan_workspace_size_rep(int64_t n, int32_t num_boxes, int64_t nnz, int64_t sources,
+                                               int64_t records, const p2p_tuning* tuning, size_t* bytes) {
+    if (!bytes || records < 0 || records >= INT32_MAX) return P2P_ERR_INVALID;
+    p2p_status st = check_sizes(n, num_boxes, n, num_boxes, sources, P2P_LAYOUT_REPETITION, 1, false);
+    if (st != P2P_OK) return st;
+    p2p_tuning t = resolve_tuning(tuning);
+    if (!tuning_valid(t)) return P2P_ERR_INVALID;
+    *bytes = plan_layout(n, num_boxes, n, num_boxes, false, sources, nnz, P2P_LAYOUT_REPETITION, 1, t, nullptr, records)
+                 .bytes;
     return P2P_OK;
 }
 

@@ -148,7 +148,7 @@ def test_apply_high_frequency(edge, layout):
                                     {"chunk": 64, "warps_per_cta": 1, "target_group": 64, "warp_boxes": -1},
                                     {"chunk": 256, "warps_per_cta": 16, "target_group": 128, "warp_boxes": -1},
                                     {"chunk": 1024, "warps_per_cta": 2, "target_group": 96, "warp_boxes": -1},
-                                    {"warp_boxes": 1}, {"warp_boxes": 2}, {"warp_boxes": 4}])
+                                    {"warp_boxes": 1}, {"warp_boxes": 4}, {"warp_boxes": 32}])
 def test_apply_tunings(tuning):
     api = _cuda()
     wl = _clustered(12000, 13)
@@ -162,12 +162,12 @@ def test_apply_tunings(tuning):
         assert plan.info["tuning"]["warp_boxes"] == want
 
 
-@pytest.mark.parametrize("warp_boxes", [1, 2, 4])
+@pytest.mark.parametrize("warp_boxes", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
 @pytest.mark.parametrize("layout", ["indexed", "redundant"])
 def test_direct_kernel(warp_boxes, kernel, layout):
-    """The direct kernel (1, 2 or 4 whole boxes per warp, sources read through the L1) on the dense cube (boxes
-    of ~64 targets: several passes per box at 8 lanes per box), a sparse sphere and the clustered assembly
+    """The direct kernel (1 - 32 whole boxes per warp, sources read through the L1) on the dense cube (boxes
+    of ~64 targets: several passes per box at 8 lanes or fewer per box), a sparse sphere and the clustered assembly
     (occupancy 1 - 128), forward and adjoint; every result row is stored once (the output starts as garbage)."""
     api = _cuda()
     kern = oracle.HELMHOLTZ if kernel == "helmholtz" else oracle.LAPLACE
