@@ -983,6 +983,67 @@ def run_tree_sweep(args):
     return 0
 
 
+def run_pieces(args):
+    """A problem cut into pieces of the size the paper recommends for its repetition kernel (Sec. 4.3: 50 000 -
+    150 000 points): sixteen unit-sphere pieces of 65 536 points (32 points per box, leaf edge a quarter
+    wavelength, Helmholtz, one RHS), applied as one graph-replayed persistent batch against sixteen separate
+    applies (each a staging launch and a pair-kernel launch) issued eagerly, and against the same sixteen applies
+    captured in one CUDA graph."""
+    import torch
+    from paper_2403_01596_gb300 import api, workloads as W
+    torch.cuda.set_device(0)
+    count, n, ng = 16, 1 << 16, 24
+    plans, lams, pairs = [], [], []
+    for g in range(count):
+        pts = torch.from_numpy(W.unit_sphere(n, 200 + g)).cuda()
+        h = 2.0 / ng
+        plans.append(api.Plan(pts, (-1.0, -1.0, -1.0), h, ng, 2 * np.pi / (4 * h), tuning={"warp_boxes": -1}))
+        lams.append(torch.from_numpy(W.strengths(n, 1, 200 + g)).cuda())
+        pairs.append(plans[-1].pair_count())
+    stream = torch.cuda.current_stream()
+    outs_sep = [torch.empty_like(l) for l in lams]
+    batch = api.Batch(plans, nrhs=1)
+    outs = batch.capture(lams)
+    med_b, _ = _events_time(batch.replay, args.ext_steps, 3, stream)
+    med_s, _ = _events_time(lambda: [p.apply(l, out=o) for p, l, o in zip(plans, lams, outs_sep)], args.ext_steps, 3,
+                            stream)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for p, l, o in zip(plans, lams, outs_sep):  # warm-up on the capture stream
+            p.apply(l, out=o)
+    stream.wait_stream(side)
+    with torch.cuda.graph(graph):
+        for p, l, o in zip(plans, lams, outs_sep):
+            p.apply(l, out=o)
+    med_g, _ = _events_time(graph.replay, args.ext_steps, 3, stream)
+    batch.replay()
+    torch.cuda.synchronize()
+    diff = max(float((o.reshape(-1) - s.reshape(-1)).abs().max() / s.abs().max()) for o, s in zip(outs, outs_sep))
+    # both against the FP64 oracle on sampled targets of two pieces
+    errs = {}
+    for g in (0, count - 1):
+        wl = W.Workload(f"piece{g}", W.unit_sphere(n, 200 + g), (-1.0, -1.0, -1.0), 2.0 / ng, ng,
+                        2 * np.pi / (4 * 2.0 / ng), 200 + g)
+        targets = _sample_targets(n, 2000, g)
+        ref, _ = _oracle_sampled(wl, lams[g].cpu().numpy(), targets)
+        errs[f"piece{g}"] = {"batch": float(_rel_l2_cols(outs[g].reshape(-1).cpu().numpy()[targets], ref).max()),
+                             "separate": float(_rel_l2_cols(outs_sep[g].reshape(-1).cpu().numpy()[targets], ref).max())}
+    P = sum(pairs)
+    line = {"metric": METRIC + " [16 pieces of 65 536 points: one batched launch vs separate applies]",
+            "value": P / med_b / 1e6, "unit": UNIT, "n_gpus": 1, "steps": args.ext_steps, "warmup": 3,
+            "ms_per_step": med_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sphere_pieces", "pieces": count, "n_points_each": n, "grid": ng, "nrhs": 1,
+                       "pairs": P, "work_items": batch.info["work_items"]},
+            "batch_graph_ms": med_b, "separate_eager_ms": med_s, "separate_graph_ms": med_g,
+            "speedup_vs_separate_eager": med_s / med_b, "speedup_vs_separate_graph": med_g / med_b,
+            "max_rel_diff_batch_vs_separate": diff, "rel_l2_vs_fp64_sampled": errs}
+    print(json.dumps(line))
+    return 0
+
+
 def run_cube(args):
     """Dense uniform cube (32 768 points, 8^3 boxes, k = 8 pi), both source layouts: device-timed applies
     (L2 flushed between them) and the full FP64 oracle on every target."""
@@ -1056,7 +1117,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tree-levels", default="5,6,7,8,9,10", help="tree_sweep: plate sizes N = 4^L")
-    ap.add_argument("--workload", choices=("sweep", "cube", "multirhs", "grad", "batched", "tree_sweep"),
+    ap.add_argument("--workload", choices=("sweep", "cube", "multirhs", "grad", "batched", "tree_sweep", "pieces"),
                     default="sweep",
                     help="sweep (default): the occupancy sweep; the others measure the extension paths")
     ap.add_argument("--scale", type=float, default=1.0, help="point-count scale of the extension workloads")
@@ -1081,6 +1142,8 @@ def main():
         return run_batched(args)
     if args.workload == "tree_sweep":
         return run_tree_sweep(args)
+    if args.workload == "pieces":
+        return run_pieces(args)
     return run_ours(args)
 
 
