@@ -102,9 +102,12 @@ typedef enum {
     P2P_PATH_AUTO = 0,        /* FP32 shared-G for nrhs < 16, tensor-core path otherwise (when available) */
     P2P_PATH_FP32_PER_RHS = 1,/* FP32; G re-evaluated for every right-hand side */
     P2P_PATH_FP32_SHARED = 2, /* FP32; each G evaluated once and applied to up to 4 RHS at a time */
-    P2P_PATH_TC_BF16X3 = 3    /* G tile and strengths split into BF16 hi + lo, 3 tcgen05 MMAs per 16
+    P2P_PATH_TC_BF16X3 = 3,   /* G tile and strengths split into BF16 hi + lo, 3 tcgen05 MMAs per 16
                                  sources, FP32 accumulation in tensor memory; plans with max_nrhs >= 16
                                  on an sm_103 device, else P2P_ERR_UNSUPPORTED */
+    P2P_PATH_TC_BF16X6 = 4    /* as P2P_PATH_TC_BF16X3 with three BF16 parts (hi + mid + lo, ~24 bits)
+                                 and the 6 MMAs whose part products are not below 2^-24 of the term:
+                                 FP32-level accuracy on the tensor cores, same availability */
 } p2p_path;
 
 /* Launch tuning of a plan (the autotuner's knobs).  Zero fields take defaults.  With
@@ -420,16 +423,17 @@ P2P_API p2p_status p2p_grad_points(const p2p_plan* plan, const void* lambda, con
 
 /*
  * Guarded apply: p2p_apply_path with every result within a relative tolerance
- * of the exact sum (the north-star's FP64 final reduction "when the relative
- * error exceeds 1e-6", made per target).  An evaluation whose terms G lambda are
+ * of the exact sum (an FP64 final evaluation wherever the FP32 result's error
+ * could exceed the tolerance, decided per target).  An evaluation whose terms G lambda are
  * each accurate to a relative delta has |out_i - exact_i| <= delta S_i with
  * S_i = sum_j |G(r_ij) lambda_j|; the call computes S (a Laplace sweep over
  * |lambda|), flags every target with delta S_i > tol |out_i| for some right-hand
  * side (the sums that cancel: S_i / |out_i| large), and re-evaluates the flagged
  * targets in FP64 on the GPU (their whole neighbourhood, every right-hand side),
- * overwriting their FP32 results.  delta: 2^-20 for the FP32 paths, 2^-14 for
- * the tensor-core path; path AUTO takes the tensor-core path only when
- * 32 * 2^-14 <= tol.  For strengths with random phases most targets have
+ * overwriting their FP32 results.  delta: 2^-20 for the FP32 paths and
+ * P2P_PATH_TC_BF16X6, 2^-14 for P2P_PATH_TC_BF16X3; path AUTO takes the FP32
+ * path for nrhs < 16 or without tensor-core support, else P2P_PATH_TC_BF16X3
+ * when 32 * 2^-14 <= tol and P2P_PATH_TC_BF16X6 below.  For strengths with random phases most targets have
  * S_i / |out_i| of 10 - 30, so tol = 1e-6 re-evaluates most of them; tol = 1e-4
  * picks out the strongly cancelling ones.
  *

@@ -32,6 +32,7 @@ P2P_PATH_AUTO = 0
 P2P_PATH_FP32_PER_RHS = 1
 P2P_PATH_FP32_SHARED = 2
 P2P_PATH_TC_BF16X3 = 3
+P2P_PATH_TC_BF16X6 = 4
 
 _lock = threading.Lock()
 _lib = None

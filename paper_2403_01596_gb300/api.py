@@ -22,7 +22,7 @@ KERNELS = {"helmholtz": C.P2P_HELMHOLTZ, "laplace": C.P2P_LAPLACE}
 LAYOUTS = {"indexed": C.P2P_LAYOUT_INDEXED, "redundant": C.P2P_LAYOUT_REDUNDANT,
            "symmetric": C.P2P_LAYOUT_SYMMETRIC, "repetition": C.P2P_LAYOUT_REPETITION}
 PATHS = {"auto": C.P2P_PATH_AUTO, "fp32_per_rhs": C.P2P_PATH_FP32_PER_RHS, "fp32_shared": C.P2P_PATH_FP32_SHARED,
-         "tc_bf16x3": C.P2P_PATH_TC_BF16X3}
+         "tc_bf16x3": C.P2P_PATH_TC_BF16X3, "tc_bf16x6": C.P2P_PATH_TC_BF16X6}
 
 
 def _stream():

@@ -449,8 +449,9 @@ cudaError_t p2p_pair_configure(p2p_plan* plan) {
 }
 
 // Entries shared with the tensor-core translation unit.
-p2p_status p2p_tc_stage(const p2p_plan* plan, const float2* lam, int32_t nrhs, int64_t ld, cudaStream_t s);
-p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t ld, int32_t adjoint,
+p2p_status p2p_tc_stage(const p2p_plan* plan, const float2* lam, int32_t nrhs, int64_t ld, int np,
+                        cudaStream_t s);
+p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t ld, int32_t adjoint, int np,
                         cudaStream_t s);
 bool p2p_tc_supported(const p2p_plan* plan, int32_t nrhs);
 
@@ -462,17 +463,20 @@ static p2p_path resolve_path(const p2p_plan* plan, int32_t nrhs, p2p_path path) 
     return path;
 }
 
+static bool is_tc(p2p_path path) { return path == P2P_PATH_TC_BF16X3 || path == P2P_PATH_TC_BF16X6; }
+static int tc_parts(p2p_path path) { return path == P2P_PATH_TC_BF16X6 ? 3 : 2; }
+
 P2P_API p2p_status p2p_apply_stage(const p2p_plan* plan, const void* lambda, int32_t nrhs, int64_t ld, p2p_path path,
                                    p2p_stream_t stream) {
     if (!plan) return P2P_ERR_INVALID;
     p2p_status st = check_apply_args(plan, lambda, plan->n > 0 ? plan : nullptr, nrhs, ld);
     if (st != P2P_OK) return st;
-    if (path < P2P_PATH_AUTO || path > P2P_PATH_TC_BF16X3) return P2P_ERR_INVALID;
+    if (path < P2P_PATH_AUTO || path > P2P_PATH_TC_BF16X6) return P2P_ERR_INVALID;
     if (plan->n == 0 || plan->n_src == 0) return P2P_OK;
     path = resolve_path(plan, nrhs, path);
-    if (path == P2P_PATH_TC_BF16X3 && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
+    if (is_tc(path) && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
-    if (path == P2P_PATH_TC_BF16X3) return p2p_tc_stage(plan, (const float2*)lambda, nrhs, ld, s);
+    if (is_tc(path)) return p2p_tc_stage(plan, (const float2*)lambda, nrhs, ld, tc_parts(path), s);
     if (plan->layout == P2P_LAYOUT_REPETITION) {
         // every target's record gets its own copy of its sources' strengths (the record head: 0)
         P2P_TRY_CUDA(stage_rows((const float2*)lambda, ld, plan->rec_src, plan->records, 1, plan->lam_buf, s),
@@ -491,16 +495,16 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
     if (!plan) return P2P_ERR_INVALID;
     p2p_status st = check_apply_args(plan, plan->n_src > 0 ? plan : nullptr, out, nrhs, ld);
     if (st != P2P_OK) return st;
-    if (path < P2P_PATH_AUTO || path > P2P_PATH_TC_BF16X3) return P2P_ERR_INVALID;
+    if (path < P2P_PATH_AUTO || path > P2P_PATH_TC_BF16X6) return P2P_ERR_INVALID;
     if (plan->n == 0) return P2P_OK;
     path = resolve_path(plan, nrhs, path);
-    if (path == P2P_PATH_TC_BF16X3 && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
+    if (is_tc(path) && !p2p_tc_supported(plan, nrhs)) return P2P_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     // a two-set plan may have target boxes without any source nearby: no item or unit writes their rows
     if (plan->two_sets)
         P2P_TRY_CUDA(cudaMemset2DAsync(out, (size_t)ld * 8, 0, (size_t)nrhs * 8, (size_t)plan->n, s), "p2p_apply/zero");
     if (plan->n_src == 0) return P2P_OK;
-    if (path == P2P_PATH_TC_BF16X3) return p2p_apply_tc(plan, (float2*)out, nrhs, ld, adjoint, s);
+    if (is_tc(path)) return p2p_apply_tc(plan, (float2*)out, nrhs, ld, adjoint, tc_parts(path), s);
     if (plan->layout == P2P_LAYOUT_REPETITION) {
         const float k = adjoint ? -plan->k : plan->k;
         const unsigned blocks = (unsigned)((plan->n + 255) / 256);

@@ -10,9 +10,9 @@
 // right-hand side with delta S_i > tol |out_i|, and re-evaluates the flagged
 // targets with FP64 arithmetic throughout (coordinates, distance, sin / cos and
 // the sum over the target's whole neighbourhood), so every result it returns
-// meets tol.  delta is the measured normwise error of the path: FP32 paths
-// 2^-20 (largest max_i |err_i| / S_i seen on the test workloads: 7.8e-7 against
-// 9.5e-7), tensor-core path 2^-14.
+// meets tol.  delta is the measured normwise error of the path: FP32 paths and
+// the three-part tensor-core path 2^-20 (largest max_i |err_i| / S_i seen on the
+// test workloads: 7.8e-7 and 5.2e-7 against 9.5e-7), hi/lo tensor-core path 2^-14.
 #include <math.h>
 
 #include "p2p_internal.cuh"
@@ -135,16 +135,17 @@ P2P_API p2p_status p2p_apply_guarded(const p2p_plan* plan, const void* lambda, v
     if (refined) *refined = 0;
     if (!plan || !(tol >= 0.0) || !isfinite(tol)) return P2P_ERR_INVALID;
     if (plan->layout == P2P_LAYOUT_SYMMETRIC) return P2P_ERR_UNSUPPORTED;  // its lists hold half neighbourhoods
-    if (path < P2P_PATH_AUTO || path > P2P_PATH_TC_BF16X3) return P2P_ERR_INVALID;
+    if (path < P2P_PATH_AUTO || path > P2P_PATH_TC_BF16X6) return P2P_ERR_INVALID;
     if (plan->n > 0 && (!work || ((uintptr_t)work & 255))) return P2P_ERR_INVALID;
     const GuardLayout L = guard_layout(plan->n, nrhs, work);
     if (plan->n > 0 && work_bytes < L.bytes) return P2P_ERR_WORKSPACE;
-    // AUTO takes the tensor-core path only where its bound leaves typical targets unflagged: random-phase sums
-    // have S_i / |out_i| of 10 - 30, so below tol = 32 * 2^-14 nearly every target would be re-evaluated in
-    // FP64 (measured: 19 999 of 20 000 at tol = 1e-4) and the FP32 path is the faster start
+    // AUTO takes the hi/lo tensor-core path only where its bound leaves typical targets unflagged: random-phase
+    // sums have S_i / |out_i| of 10 - 30, so below tol = 32 * 2^-14 nearly every target would be re-evaluated in
+    // FP64 (measured: 19 999 of 20 000 at tol = 1e-4); there the three-part path, with the FP32 paths' bound and
+    // faster than them from 16 RHS on, is the start
     if (path == P2P_PATH_AUTO) {
         const bool tc = nrhs >= 16 && p2p_tc_supported(plan, nrhs);
-        path = (tc && 32.0 * kDeltaTc <= tol) ? P2P_PATH_TC_BF16X3 : P2P_PATH_FP32_SHARED;
+        path = !tc ? P2P_PATH_FP32_SHARED : (32.0 * kDeltaTc <= tol ? P2P_PATH_TC_BF16X3 : P2P_PATH_TC_BF16X6);
     }
     p2p_status st = p2p_apply_path(plan, lambda, out, nrhs, ld, adjoint, path, stream);
     if (st != P2P_OK || plan->n == 0 || plan->n_src == 0) return st;

@@ -13,7 +13,8 @@
 // padded M rows and no negated copy).  G is formed on the CUDA cores in FP32
 // (rsqrt, sincos), both operands are split x = hi + lo into BF16, and three MMAs
 // (hi.hi + hi.lo + lo.hi, kind::f16, FP32 accumulation in TMEM) keep the product
-// error near 2^-16.
+// error near 2^-16.  With NP = 3 parts (hi + mid + lo, ~24 bits) six MMAs take
+// every part product p.q with p + q < 3, and the product error is near 2^-24.
 //
 // Group records.  The A operand of a source group does not depend on the target
 // box, so a pass per apply (k_tc_pack) writes every group's hi and lo images,
@@ -57,7 +58,8 @@ namespace {
 
 constexpr float kInv4Pi = 0.0795774715459476679f;
 constexpr int kSrcGroup = 16;          // sources per stage (MMA K)
-constexpr int kImage = 8192;           // hi + lo images of one 128 x 16 A operand
+constexpr int kPart = 4096;            // one BF16 image of a 128 x 16 A operand
+constexpr int kImage = 2 * kPart;      // hi + lo images (the operand self-check)
 constexpr int kLbo = 128, kSbo = 256;  // core-matrix strides (K direction, 8-row groups)
 constexpr int kSetCols = 256;          // TMEM columns of one unit buffer (an accumulator per G set)
 // G sets (independent producer -> G -> MMA chains; 2 or 4, the group lists are
@@ -214,6 +216,20 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
     lo = *reinterpret_cast<uint32_t*>(&l);
 }
 
+// x = hi + mid + lo with three BF16 parts (each the round-to-nearest of what the
+// previous parts leave), two values per 32-bit word: the parts carry ~24 bits.
+__device__ __forceinline__ void split3(float a, float b, uint32_t& hi, uint32_t& mid, uint32_t& lo) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const float ra = a - hf.x, rb = b - hf.y;
+    __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+    const float2 mf = __bfloat1622float2(m);
+    __nv_bfloat162 l = __floats2bfloat162_rn(ra - mf.x, rb - mf.y);
+    hi = *reinterpret_cast<uint32_t*>(&h);
+    mid = *reinterpret_cast<uint32_t*>(&m);
+    lo = *reinterpret_cast<uint32_t*>(&l);
+}
+
 __device__ __forceinline__ void split1(float a, uint16_t& hi, uint16_t& lo) {
     __nv_bfloat16 h = __float2bfloat16_rn(a);
     __nv_bfloat16 l = __float2bfloat16_rn(a - __bfloat162float(h));
@@ -257,17 +273,50 @@ __device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo
     }
 }
 
+// Splits n values (n = 2, 4 or 8, consecutive K elements of one row) into NP
+// BF16 parts (2: hi, lo; 3: hi, mid, lo) stored at `off` in the images starting
+// at part0, part_bytes apart.
+template <int NP, int N>
+__device__ __forceinline__ void store_parts(unsigned char* part0, int part_bytes, int off, const float (&v)[N]) {
+    if constexpr (NP == 2) {
+        store_split<N>(part0, part0 + part_bytes, off, v);
+    } else if constexpr (N == 1) {
+        uint32_t h, m, l;
+        split3(v[0], 0.f, h, m, l);
+        *reinterpret_cast<uint16_t*>(part0 + off) = (uint16_t)(h & 0xffffu);
+        *reinterpret_cast<uint16_t*>(part0 + part_bytes + off) = (uint16_t)(m & 0xffffu);
+        *reinterpret_cast<uint16_t*>(part0 + 2 * part_bytes + off) = (uint16_t)(l & 0xffffu);
+    } else {
+        uint32_t h[N / 2], m[N / 2], l[N / 2];
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) split3(v[2 * i], v[2 * i + 1], h[i], m[i], l[i]);
+        unsigned char* dst[3] = {part0, part0 + part_bytes, part0 + 2 * part_bytes};
+        const uint32_t* src[3] = {h, m, l};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if constexpr (N == 2) {
+                *reinterpret_cast<uint32_t*>(dst[q] + off) = src[q][0];
+            } else if constexpr (N == 4) {
+                *reinterpret_cast<uint2*>(dst[q] + off) = make_uint2(src[q][0], src[q][1]);
+            } else {
+                *reinterpret_cast<uint4*>(dst[q] + off) = make_uint4(src[q][0], src[q][1], src[q][2], src[q][3]);
+            }
+        }
+    }
+}
+
 // ----------------------------------------------------------- strength pre-pack --
 
-// Bytes of one group record: the hi and lo images of every block of 64 RHS,
+// Bytes of one group record: the NP BF16 part images of every block of 64 RHS,
 // then the group's 16 source coordinates (w = 1 marks a padding slot).
-__host__ __device__ inline int record_bytes(int rb_count) { return rb_count * kImage + kSrcGroup * 16; }
+__host__ __device__ inline int record_bytes(int rb_count, int np) { return rb_count * np * kPart + kSrcGroup * 16; }
 
 // Block (group g, RHS block rb), 128 threads: thread (r = tid % 64, o = tid / 64)
 // splits Re and Im lambda of RHS rb * 64 + r for sources 8o .. 8o + 7 of the
-// group into rows r and 64 + r of the group's hi and lo images.  Sources past the
+// group into rows r and 64 + r of the group's NP part images.  Sources past the
 // box's end and RHS past nrhs are zero.  Block row rb = 0 also writes the
 // coordinates.
+template <int NP>
 __global__ void __launch_bounds__(128) k_tc_pack(const float2* __restrict__ lam, int64_t ld, int32_t nrhs,
                                                  const int32_t* __restrict__ perm, const int32_t* __restrict__ box_ptr,
                                                  const float4* __restrict__ xs, const int32_t* __restrict__ gstart,
@@ -284,10 +333,11 @@ __global__ void __launch_bounds__(128) k_tc_pack(const float2* __restrict__ lam,
     const int j = g - gstart[c];
     const int s0 = box_ptr[c] + j * kSrcGroup;
     const int cnt = min(kSrcGroup, box_ptr[c + 1] - s0);
-    unsigned char* rec = pack + (int64_t)g * record_bytes(rb_count);
+    unsigned char* rec = pack + (int64_t)g * record_bytes(rb_count, NP);
     if (rb == 0 && threadIdx.x < kSrcGroup) {
         const int k = threadIdx.x;
-        reinterpret_cast<float4*>(rec + rb_count * kImage)[k] = k < cnt ? xs[s0 + k] : make_float4(0.f, 0.f, 0.f, 1.f);
+        reinterpret_cast<float4*>(rec + rb_count * NP * kPart)[k] =
+            k < cnt ? xs[s0 + k] : make_float4(0.f, 0.f, 0.f, 1.f);
     }
     const int r = threadIdx.x & 63, o = threadIdx.x >> 6;
     const int rr = rb * 64 + r;
@@ -300,9 +350,9 @@ __global__ void __launch_bounds__(128) k_tc_pack(const float2* __restrict__ lam,
         re[e] = v.x;
         im[e] = v.y;
     }
-    unsigned char* img = rec + rb * kImage;
-    store_split<8>(img, img + kImage / 2, op_off(r, 8 * o), re);
-    store_split<8>(img, img + kImage / 2, op_off(64 + r, 8 * o), im);
+    unsigned char* img = rec + rb * NP * kPart;
+    store_parts<NP, 8>(img, kPart, op_off(r, 8 * o), re);
+    store_parts<NP, 8>(img, kPart, op_off(64 + r, 8 * o), im);
 }
 
 // ------------------------------------------------------------------ main kernel --
@@ -324,19 +374,22 @@ struct TcArgs {
     int32_t nb;
     int32_t slots;                 // pipeline slots per G set
     int32_t slot_bytes;
+    int32_t np;                    // BF16 parts per operand: 2 (hi, lo) or 3 (hi, mid, lo)
     float k;
     unsigned int* status;
     uint32_t wait_limit;           // polls of every pipeline wait (kWaitLimit unless a self-check lowers it)
 };
 
-// Slot layout: group record (A images, source coordinates), the unit's targets,
-// B hi and lo (2T rows each, T <= tg), metadata.
-__host__ __device__ inline int slot_t_off(int rb_count) { return record_bytes(rb_count); }
-__host__ __device__ inline int slot_b_off(int rb_count, int tg) { return record_bytes(rb_count) + tg * 16; }
-__host__ __device__ inline int slot_b_half(int tg) { return (2 * tg / 8) * kSbo; }
-__host__ __device__ inline int slot_meta_off(int rb_count, int tg) { return slot_b_off(rb_count, tg) + 2 * slot_b_half(tg); }
-__host__ __device__ inline int slot_bytes_for(int rb_count, int tg) {
-    return (slot_meta_off(rb_count, tg) + 16 + 1023) / 1024 * 1024;
+// Slot layout: group record (A part images, source coordinates), the unit's
+// targets, the NP parts of B (2T rows each, T <= tg), metadata.
+__host__ __device__ inline int slot_t_off(int rb_count, int np) { return record_bytes(rb_count, np); }
+__host__ __device__ inline int slot_b_off(int rb_count, int tg, int np) { return record_bytes(rb_count, np) + tg * 16; }
+__host__ __device__ inline int slot_b_half(int tg) { return (2 * tg / 8) * kSbo; }  // bytes of one B part
+__host__ __device__ inline int slot_meta_off(int rb_count, int tg, int np) {
+    return slot_b_off(rb_count, tg, np) + np * slot_b_half(tg);
+}
+__host__ __device__ inline int slot_bytes_for(int rb_count, int tg, int np) {
+    return (slot_meta_off(rb_count, tg, np) + 16 + 1023) / 1024 * 1024;
 }
 constexpr int kEpiBytes = 8 * 64 * 8;  // epilogue exchange: 8 targets x 64 RHS x complex
 __host__ __device__ inline int tc_smem_bytes(int slots, int slot_bytes) {
@@ -410,8 +463,8 @@ __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, i
     const bool active = lane == 0;
     Ring r{0, 0u};
     int64_t staged = 0;  // stages this producer has armed (their copies may still be in flight)
-    const uint32_t rec = (uint32_t)record_bytes(a.rb_count);
-    const int t_off = slot_t_off(a.rb_count), meta_off = slot_meta_off(a.rb_count, a.tg);
+    const uint32_t rec = (uint32_t)record_bytes(a.rb_count, a.np);
+    const int t_off = slot_t_off(a.rb_count, a.np), meta_off = slot_meta_off(a.rb_count, a.tg, a.np);
     bool failed = false;
     auto slot_base = [&](int slot) { return sm.slots + (size_t)(set * a.slots + slot) * a.slot_bytes; };
     for (int64_t u = blockIdx.x; u < units && !failed; u += gridDim.x) {
@@ -486,9 +539,9 @@ __device__ void run_producer(const TcArgs& a, const TcSmem& sm, int64_t units, i
 // For SP >= 2 the sources go in pairs through the packed two-lane FP32
 // instructions (each rounding as its scalar counterpart); rsqrt and sincos
 // stay per pair.  r = 0 and padding slots (w = 1) give 0.
-template <int KERN, int SP>
+template <int KERN, int SP, int NP>
 __device__ __forceinline__ void g_tile(const float4* __restrict__ sx, float4 tx, int t, int h, int T,
-                                       unsigned char* b_hi, unsigned char* b_lo, float k) {
+                                       unsigned char* b_part0, int b_part_bytes, float k) {
     float re[SP], im[SP];
     if constexpr (SP == 1) {
         const float4 p = sx[h];
@@ -534,16 +587,16 @@ __device__ __forceinline__ void g_tile(const float4* __restrict__ sx, float4 tx,
             }
         }
     }
-    store_split<SP>(b_hi, b_lo, op_off(t, h * SP), re);
-    store_split<SP>(b_hi, b_lo, op_off(T + t, h * SP), im);
+    store_parts<NP, SP>(b_part0, b_part_bytes, op_off(t, h * SP), re);
+    store_parts<NP, SP>(b_part0, b_part_bytes, op_off(T + t, h * SP), im);
 }
 
-template <int KERN, bool LIMITED>
+template <int KERN, bool LIMITED, int NP>
 __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
     volatile int* abort = sm.abort;
     const uint32_t wlim = LIMITED ? a.wait_limit : kWaitLimit;
-    const int t_off = slot_t_off(a.rb_count), b_off = slot_b_off(a.rb_count, a.tg);
-    const int b_half = slot_b_half(a.tg), meta_off = slot_meta_off(a.rb_count, a.tg);
+    const int t_off = slot_t_off(a.rb_count, NP), b_off = slot_b_off(a.rb_count, a.tg, NP);
+    const int b_half = slot_b_half(a.tg), meta_off = slot_meta_off(a.rb_count, a.tg, NP);
     // this thread's task in the current unit: target t, sources h sp .. h sp + sp - 1 (set at the unit's first quad)
     float4 tx = make_float4(0.f, 0.f, 0.f, 0.f);
     int T = 8, sp = 1, t = 0, h = 0;
@@ -576,14 +629,13 @@ __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
             }
         }
         if (m.x >= 0) {
-            const float4* sx = reinterpret_cast<const float4*>(base + kImage * a.rb_count);
+            const float4* sx = reinterpret_cast<const float4*>(base + NP * kPart * a.rb_count);
             if (act) {
-                unsigned char* b_hi = base + b_off;
-                unsigned char* b_lo = b_hi + b_half;
-                if (sp == 8) g_tile<KERN, 8>(sx, tx, t, h, T, b_hi, b_lo, a.k);
-                else if (sp == 4) g_tile<KERN, 4>(sx, tx, t, h, T, b_hi, b_lo, a.k);
-                else if (sp == 2) g_tile<KERN, 2>(sx, tx, t, h, T, b_hi, b_lo, a.k);
-                else g_tile<KERN, 1>(sx, tx, t, h, T, b_hi, b_lo, a.k);
+                unsigned char* b0 = base + b_off;
+                if (sp == 8) g_tile<KERN, 8, NP>(sx, tx, t, h, T, b0, b_half, a.k);
+                else if (sp == 4) g_tile<KERN, 4, NP>(sx, tx, t, h, T, b0, b_half, a.k);
+                else if (sp == 2) g_tile<KERN, 2, NP>(sx, tx, t, h, T, b0, b_half, a.k);
+                else g_tile<KERN, 1, NP>(sx, tx, t, h, T, b0, b_half, a.k);
             }
             fence_async_smem();
         }
@@ -593,12 +645,12 @@ __device__ void run_gset(const TcArgs& a, const TcSmem& sm, int set, int i) {
 }
 
 // ---- MMA issuer of a set (one thread) ----
-template <bool LIMITED>
+template <bool LIMITED, int NP>
 __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int set) {
     volatile int* abort = sm.abort;
     const uint32_t wlim = LIMITED ? a.wait_limit : kWaitLimit;
-    const int b_off = slot_b_off(a.rb_count, a.tg), b_half = slot_b_half(a.tg);
-    const int meta_off = slot_meta_off(a.rb_count, a.tg);
+    const int b_off = slot_b_off(a.rb_count, a.tg, NP), b_half = slot_b_half(a.tg);
+    const int meta_off = slot_meta_off(a.rb_count, a.tg, NP);
     const uint32_t acc_cols = (uint32_t)(a.rb_count * 2 * a.tg);
     Ring r{0, 0u};
     uint32_t unit = 0;
@@ -630,16 +682,24 @@ __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int se
             const int T = (m.z + 7) & ~7;
             const uint32_t idesc = idesc_bf16_f32(2 * T);
             const uint32_t sbase = smem_u32(base);
-            const uint64_t db_hi = smem_desc(sbase + (uint32_t)b_off);
-            const uint64_t db_lo = db_hi + (uint64_t)(b_half >> 4);
+            // descriptors address 16-byte units: part p of an operand is p * bytes-per-part / 16 further
+            const uint64_t db0 = smem_desc(sbase + (uint32_t)b_off);
+            const uint64_t db_step = (uint64_t)(b_half >> 4);
             const uint32_t d0 = tmem + ub * kSetCols + (uint32_t)set * acc_cols;
             for (int rb = 0; rb < a.rb_count; ++rb) {
-                const uint64_t da_hi = smem_desc(sbase + (uint32_t)rb * kImage);
-                const uint64_t da_lo = da_hi + (uint64_t)((kImage / 2) >> 4);
+                const uint64_t da0 = smem_desc(sbase + (uint32_t)(rb * NP * kPart));
+                const uint64_t da_step = (uint64_t)(kPart >> 4);
                 const uint32_t d = d0 + (uint32_t)(rb * 2 * a.tg);
-                mma_bf16(d, da_hi, db_hi, idesc, acc_started ? 1u : 0u);
-                mma_bf16(d, da_hi, db_lo, idesc, 1u);
-                mma_bf16(d, da_lo, db_hi, idesc, 1u);
+                // every product of parts p (of lambda) and q (of G) with p + q < NP: 3 MMAs for hi / lo,
+                // 6 for hi / mid / lo (the dropped products are below 2^-8 NP of the leading one)
+                mma_bf16(d, da0, db0, idesc, acc_started ? 1u : 0u);
+                mma_bf16(d, da0, db0 + db_step, idesc, 1u);
+                mma_bf16(d, da0 + da_step, db0, idesc, 1u);
+                if constexpr (NP == 3) {
+                    mma_bf16(d, da0, db0 + 2 * db_step, idesc, 1u);
+                    mma_bf16(d, da0 + da_step, db0 + db_step, idesc, 1u);
+                    mma_bf16(d, da0 + 2 * da_step, db0, idesc, 1u);
+                }
             }
             acc_started = true;
         }
@@ -738,7 +798,8 @@ __device__ void run_epilogue(const TcArgs& a, const TcSmem& sm, uint32_t tmem, i
 }
 
 // LIMITED: the waits poll at most a.wait_limit times (the abort-path self-check); otherwise kWaitLimit.
-template <int KERN, bool LIMITED>
+// NP: BF16 parts per operand (2: three MMAs per stage, 3: six).
+template <int KERN, bool LIMITED, int NP>
 __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -766,9 +827,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_p2p_tc(const __grid_constant__ 
         run_producer<LIMITED>(a, sm, units, warp, lane);
     } else if (warp < kMmaWarp0) {
         const int gw = warp - kGWarp0;
-        run_gset<KERN, LIMITED>(a, sm, gw / kSetWarps, (gw % kSetWarps) * 32 + lane);
+        run_gset<KERN, LIMITED, NP>(a, sm, gw / kSetWarps, (gw % kSetWarps) * 32 + lane);
     } else if (warp < kEpiWarp0) {
-        if (lane == 0) run_mma<LIMITED>(a, sm, tmem, warp - kMmaWarp0);
+        if (lane == 0) run_mma<LIMITED, NP>(a, sm, tmem, warp - kMmaWarp0);
     } else {
         run_epilogue<LIMITED>(a, sm, tmem, units, warp, lane);
     }
@@ -870,13 +931,13 @@ struct TcShape {
     int rb_count, tg, slots, slot_bytes, smem;
 };
 
-TcShape tc_shape(int32_t nrhs, int optin) {
+TcShape tc_shape(int32_t nrhs, int optin, int np) {
     TcShape s;
     s.rb_count = (nrhs + 63) / 64;
     // one accumulator per G set (rb_count blocks x 2T columns) in each of two unit buffers
     s.tg = (kSetCols / (2 * kSets * s.rb_count)) / 8 * 8;
     if (s.tg > 64) s.tg = 64;
-    s.slot_bytes = slot_bytes_for(s.rb_count, s.tg);
+    s.slot_bytes = slot_bytes_for(s.rb_count, s.tg, np);
     s.slots = 8;
     while (s.slots > 1 && tc_smem_bytes(s.slots, s.slot_bytes) > optin) --s.slots;
     s.smem = tc_smem_bytes(s.slots, s.slot_bytes);
@@ -888,10 +949,11 @@ TcShape tc_shape(int32_t nrhs, int optin) {
 
 }  // namespace
 
+// Room for the records of either split (sized for three parts).
 size_t p2p_tc_pack_bytes(int64_t n, int32_t nb, int32_t max_nrhs) {
     if (max_nrhs < 16) return 0;
     const int64_t groups = n / kSrcGroup + nb;
-    return (size_t)groups * (size_t)record_bytes((max_nrhs + 63) / 64);
+    return (size_t)groups * (size_t)record_bytes((max_nrhs + 63) / 64, 3);
 }
 
 bool p2p_tc_supported(const p2p_plan* plan, int32_t nrhs) {
@@ -904,25 +966,27 @@ bool p2p_tc_supported(const p2p_plan* plan, int32_t nrhs) {
 }
 
 // Stage: the group records (strength images from original-order lambda via perm, coordinates).
-p2p_status p2p_tc_stage(const p2p_plan* plan, const float2* lam, int32_t nrhs, int64_t ld, cudaStream_t s) {
+p2p_status p2p_tc_stage(const p2p_plan* plan, const float2* lam, int32_t nrhs, int64_t ld, int np,
+                        cudaStream_t s) {
     if (plan->n == 0 || plan->tc_groups == 0) return P2P_OK;
     const int rb_count = (nrhs + 63) / 64;
     dim3 grid((unsigned)plan->tc_groups, (unsigned)rb_count);
     // the group records are built over the SOURCE boxes
-    k_tc_pack<<<grid, 128, 0, s>>>(lam, ld, nrhs, plan->src_perm, plan->src_box_ptr, plan->xs_src, plan->tc_gstart,
-                                   plan->nbs, rb_count, plan->tc_pack);
+    auto pack = np == 3 ? k_tc_pack<3> : k_tc_pack<2>;
+    pack<<<grid, 128, 0, s>>>(lam, ld, nrhs, plan->src_perm, plan->src_box_ptr, plan->xs_src, plan->tc_gstart,
+                              plan->nbs, rb_count, plan->tc_pack);
     P2P_CHECK_LAUNCH("p2p_apply_stage/tc_pack");
     return P2P_OK;
 }
 
-p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t ld, int32_t adjoint,
+p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t ld, int32_t adjoint, int np,
                         cudaStream_t s) {
     if (plan->n == 0) return P2P_OK;
     int dev = 0, optin = 0, sms = 0;
     P2P_TRY_CUDA(cudaGetDevice(&dev), "p2p_apply_tc");
     P2P_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "p2p_apply_tc");
     P2P_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "p2p_apply_tc");
-    const TcShape sh = tc_shape(nrhs, optin);
+    const TcShape sh = tc_shape(nrhs, optin, np);
     if (sh.smem > optin) {
         set_message("p2p_apply_tc: the tensor-core pipeline does not fit in shared memory");
         return P2P_ERR_UNSUPPORTED;
@@ -944,12 +1008,20 @@ p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t
     a.nb = plan->nb;
     a.slots = sh.slots;
     a.slot_bytes = sh.slot_bytes;
+    a.np = np;
     a.k = adjoint ? -plan->k : plan->k;
     a.status = plan->status;
     a.wait_limit = plan->tc_wait_polls < 0 ? kWaitLimit : (uint32_t)plan->tc_wait_polls;
     const bool limited = plan->tc_wait_polls >= 0;
-    auto kern = plan->kernel == P2P_LAPLACE ? (limited ? k_p2p_tc<P2P_LAPLACE, true> : k_p2p_tc<P2P_LAPLACE, false>)
-                                            : (limited ? k_p2p_tc<P2P_HELMHOLTZ, true> : k_p2p_tc<P2P_HELMHOLTZ, false>);
+    void (*kern)(TcArgs) = nullptr;
+    const bool lap = plan->kernel == P2P_LAPLACE;
+    if (np == 3) {
+        kern = lap ? (limited ? k_p2p_tc<P2P_LAPLACE, true, 3> : k_p2p_tc<P2P_LAPLACE, false, 3>)
+                   : (limited ? k_p2p_tc<P2P_HELMHOLTZ, true, 3> : k_p2p_tc<P2P_HELMHOLTZ, false, 3>);
+    } else {
+        kern = lap ? (limited ? k_p2p_tc<P2P_LAPLACE, true, 2> : k_p2p_tc<P2P_LAPLACE, false, 2>)
+                   : (limited ? k_p2p_tc<P2P_HELMHOLTZ, true, 2> : k_p2p_tc<P2P_HELMHOLTZ, false, 2>);
+    }
     P2P_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem), "p2p_apply_tc");
     const int64_t units = (int64_t)a.nb * a.ngrp;
     const int grid = (int)std::min<int64_t>(units, sms);

@@ -102,14 +102,15 @@ def test_guarded_apply_several_rhs_adjoint_and_tensor_cores():
     ref = oracle.p2p(wl.points, lam[:, :3], wl.lo, wl.h, wl.ng, wl.k, adjoint=True)
     out, refined = plan.apply_guarded(lam_d[:, :3].contiguous(), tol=1e-5, adjoint=True)
     assert _rel(out.cpu().numpy(), ref).max() <= 1e-5 and refined > 0
-    # 16 right-hand sides: the tensor-core path with its own bound 2^-14 (explicit path), and AUTO, which at
-    # tol 1e-4 starts from the FP32 path instead (the tensor-core bound would flag nearly every target)
+    # 16 right-hand sides: the hi/lo tensor-core path with its own bound 2^-14 (explicit path), the three-part
+    # path with the FP32 bound 2^-20, and AUTO, which at tol 1e-4 starts from the three-part path (the hi/lo
+    # bound would flag nearly every target)
     ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
-    for path in ("tc_bf16x3", "auto"):
+    for path in ("tc_bf16x3", "tc_bf16x6", "auto"):
         out, refined = plan.apply_guarded(lam_d, tol=1e-4, path=path)
         rel = _rel(out.cpu().numpy(), ref)
         print(f"16 RHS, path {path}, tol 1e-4: {refined} targets in FP64, worst relative error {rel.max():.2e}")
         assert rel.max() <= 1e-4 and rel[chosen, 0].max() <= 2e-7
-        if path == "auto":
+        if path != "tc_bf16x3":
             assert refined < wl.n // 10
     assert plan.async_status() == 0

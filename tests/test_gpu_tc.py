@@ -3,6 +3,8 @@
 Tolerance: relative L2 error per right-hand side <= 1e-5, the bound the FP32
 path meets; the three-product BF16 split (hi.hi + hi.lo + lo.hi) leaves a
 per-product error near 2^-17 that averages down over the neighbourhood sums.
+The six-product split (hi + mid + lo) is held to the FP32 path's per-target
+bound as well: |err_i| <= 2^-20 S_i with S_i = sum_j |G(r_ij) lambda_j|.
 """
 import numpy as np
 import pytest
@@ -52,40 +54,47 @@ def _sphere(n, ng, seed):
     return W.Workload("sphere", p, (-1.0, -1.0, -1.0), h, ng, 2 * np.pi / (5 * h), seed)
 
 
+TC_PATHS = ["tc_bf16x3", "tc_bf16x6"]
+
+
+@pytest.mark.parametrize("path", TC_PATHS)
 @pytest.mark.parametrize("nrhs", [16, 24, 64])
 @pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
-def test_tc_apply_parity(nrhs, kernel):
+def test_tc_apply_parity(nrhs, kernel, path):
     api = _api()
     wl = _sphere(20000, 24, 31)
     lam = W.strengths(wl.n, nrhs, 31)
     k = wl.k if kernel == "helmholtz" else 0.0
     plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, k, kernel=kernel, max_nrhs=nrhs)
-    out = plan.apply(torch.from_numpy(lam).cuda(), path="tc_bf16x3").cpu().numpy()
+    out = plan.apply(torch.from_numpy(lam).cuda(), path=path).cpu().numpy()
     assert plan.async_status() == 0
     ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, k,
                      kernel=oracle.HELMHOLTZ if kernel == "helmholtz" else oracle.LAPLACE)
     err = rel_l2(out, ref)
-    print(f"{kernel} nrhs={nrhs} tensor-core rel-L2 max {err.max():.3e}")
+    print(f"{kernel} nrhs={nrhs} {path} rel-L2 max {err.max():.3e}")
     assert err.max() <= TOL, err
 
 
-@pytest.mark.parametrize("nrhs", [96, 200])
-def test_tc_several_rhs_blocks(nrhs):
-    """More than 64 right-hand sides: several RHS blocks share each G tile."""
+@pytest.mark.parametrize("path", TC_PATHS)
+@pytest.mark.parametrize("nrhs", [96, 200, 256])
+def test_tc_several_rhs_blocks(nrhs, path):
+    """More than 64 right-hand sides: several RHS blocks share each G tile (at 256 and three parts, one
+    pipeline slot per set)."""
     api = _api()
     wl = _sphere(12000, 20, 37)
     lam = W.strengths(wl.n, nrhs, 37)
     plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, wl.k, max_nrhs=nrhs)
-    out = plan.apply(torch.from_numpy(lam).cuda(), path="tc_bf16x3").cpu().numpy()
+    out = plan.apply(torch.from_numpy(lam).cuda(), path=path).cpu().numpy()
     assert plan.async_status() == 0
     ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, wl.k)
     err = rel_l2(out, ref)
-    print(f"nrhs={nrhs} tensor-core rel-L2 max {err.max():.3e}")
+    print(f"nrhs={nrhs} {path} rel-L2 max {err.max():.3e}")
     assert err.max() <= TOL, err
 
 
+@pytest.mark.parametrize("path", TC_PATHS)
 @pytest.mark.parametrize("n", [1, 2, 7, 33, 500])
-def test_tc_tiny_plans_and_single_rhs(n):
+def test_tc_tiny_plans_and_single_rhs(n, path):
     """Few points: units with fewer source groups than G sets (padding entries), boxes of one point, and a
     single right-hand side through the tensor-core path (RHS rows padded with zeros)."""
     api = _api()
@@ -96,7 +105,7 @@ def test_tc_tiny_plans_and_single_rhs(n):
     plan = api.Plan(torch.from_numpy(pts).cuda(), lo, h, ng, k, max_nrhs=16)
     for nrhs in (1, 16):
         lam = W.strengths(n, nrhs, n + nrhs).reshape(n, nrhs)
-        out = plan.apply(torch.from_numpy(lam).cuda(), path="tc_bf16x3").cpu().numpy().reshape(n, nrhs)
+        out = plan.apply(torch.from_numpy(lam).cuda(), path=path).cpu().numpy().reshape(n, nrhs)
         assert plan.async_status() == 0
         ref = oracle.p2p(pts, lam, lo, h, ng, k).reshape(n, nrhs)
         if not np.linalg.norm(ref):
@@ -152,3 +161,31 @@ def test_tc_full_size_ellipsoid_sampled():
     targets = np.random.default_rng(21).choice(wl.n, 400, replace=False)
     ref = oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, wl.k)
     assert rel_l2(out[targets], ref).max() <= TOL
+
+
+@pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
+def test_tc_six_products_meet_fp32_bound(kernel):
+    """Per target and RHS, |err| / S_i of the six-product path stays under the FP32 path's 2^-20 (the
+    three-product path's own bound is 2^-14), and its adjoint as well.  S_i is the Laplace sum of |lambda|
+    (|exp(ikr)| = 1)."""
+    api = _api()
+    wl = _sphere(20000, 24, 41)
+    nrhs = 32
+    lam = W.strengths(wl.n, nrhs, 41)
+    # the plan holds k in float32: the oracle takes the same value, so the bound sees arithmetic error only
+    k = float(np.float32(wl.k)) if kernel == "helmholtz" else 0.0
+    kid = oracle.HELMHOLTZ if kernel == "helmholtz" else oracle.LAPLACE
+    plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, k, kernel=kernel, max_nrhs=nrhs)
+    targets = np.random.default_rng(41).choice(wl.n, 600, replace=False)
+    S = oracle.p2p_targets(wl.points, np.abs(lam).astype(np.float64), targets, wl.lo, wl.h, wl.ng, 0.0,
+                           kernel=oracle.LAPLACE).real
+    for adjoint in (False, True):
+        ref = oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, k, kernel=kid, adjoint=adjoint)
+        worst = {}
+        for path in TC_PATHS:
+            out = plan.apply(torch.from_numpy(lam).cuda(), adjoint=adjoint, path=path).cpu().numpy()
+            assert plan.async_status() == 0
+            worst[path] = float((np.abs(out[targets] - ref) / S).max())
+        print(f"{kernel} adjoint={adjoint} max |err| / S: {worst}")
+        assert worst["tc_bf16x6"] <= 2.0 ** -20, worst
+        assert worst["tc_bf16x3"] <= 2.0 ** -14, worst
