@@ -686,7 +686,7 @@ def measure_multirhs(scale, steps, samples, free_first=()):
     t_tc = kern_ms * 1e-3                                                 # the pipelined kernel alone
     sizes = torch.diff(plan.structure.box_ptr.long())
     groups = int(((sizes + 15) // 16).sum().item())                      # 16-source groups of the pre-pack
-    record = ((nrhs + 63) // 64) * 8192 + 16 * 16                        # BF16 hi/lo images + coordinates
+    record = ((nrhs + 63) // 64) * (8192 + 16 * 16)                      # per 64-RHS chunk: hi/lo images + coordinates
     pack_bytes = wl.n * (nrhs * 8 + 16) + groups * record                 # strengths, coordinates read; records written
     rec = {"workload": "ellipsoid211_multirhs", "n_points": wl.n, "grid": wl.ng, "nrhs": nrhs, "pairs": P,
            "boxes": plan.num_boxes, "paths": res, "async_status": status,

@@ -311,16 +311,21 @@ __device__ __forceinline__ void store_parts(unsigned char* part0, int part_bytes
 // then the group's 16 source coordinates (w = 1 marks a padding slot).
 __host__ __device__ inline int record_bytes(int rb_count, int np) { return rb_count * np * kPart + kSrcGroup * 16; }
 
+// The records of one launch (a chunk of rb_launch RHS blocks) are contiguous:
+// chunk c starts chunk_bytes * c into the buffer, group g's record
+// record_bytes(rb_launch, NP) * g into the chunk.
+//
 // Block (group g, RHS block rb), 128 threads: thread (r = tid % 64, o = tid / 64)
 // splits Re and Im lambda of RHS rb * 64 + r for sources 8o .. 8o + 7 of the
-// group into rows r and 64 + r of the group's NP part images.  Sources past the
-// box's end and RHS past nrhs are zero.  Block row rb = 0 also writes the
-// coordinates.
+// group into rows r and 64 + r of the group's NP part images in its chunk's
+// record.  Sources past the box's end and RHS past nrhs are zero.  The first
+// block of each chunk also writes the record's coordinates.
 template <int NP>
 __global__ void __launch_bounds__(128) k_tc_pack(const float2* __restrict__ lam, int64_t ld, int32_t nrhs,
                                                  const int32_t* __restrict__ perm, const int32_t* __restrict__ box_ptr,
                                                  const float4* __restrict__ xs, const int32_t* __restrict__ gstart,
-                                                 int32_t nb, int32_t rb_count, unsigned char* __restrict__ pack) {
+                                                 int32_t nb, int32_t rb_launch, int64_t chunk_bytes,
+                                                 unsigned char* __restrict__ pack) {
     const int g = blockIdx.x, rb = blockIdx.y;
     // box of group g: the last c with gstart[c] <= g
     int lo = 0, hi = nb - 1;
@@ -333,10 +338,11 @@ __global__ void __launch_bounds__(128) k_tc_pack(const float2* __restrict__ lam,
     const int j = g - gstart[c];
     const int s0 = box_ptr[c] + j * kSrcGroup;
     const int cnt = min(kSrcGroup, box_ptr[c + 1] - s0);
-    unsigned char* rec = pack + (int64_t)g * record_bytes(rb_count, NP);
-    if (rb == 0 && threadIdx.x < kSrcGroup) {
+    const int lb = rb % rb_launch;
+    unsigned char* rec = pack + (rb / rb_launch) * chunk_bytes + (int64_t)g * record_bytes(rb_launch, NP);
+    if (lb == 0 && threadIdx.x < kSrcGroup) {
         const int k = threadIdx.x;
-        reinterpret_cast<float4*>(rec + rb_count * NP * kPart)[k] =
+        reinterpret_cast<float4*>(rec + rb_launch * NP * kPart)[k] =
             k < cnt ? xs[s0 + k] : make_float4(0.f, 0.f, 0.f, 1.f);
     }
     const int r = threadIdx.x & 63, o = threadIdx.x >> 6;
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(128) k_tc_pack(const float2* __restrict__ lam,
         re[e] = v.x;
         im[e] = v.y;
     }
-    unsigned char* img = rec + rb * NP * kPart;
+    unsigned char* img = rec + lb * NP * kPart;
     store_parts<NP, 8>(img, kPart, op_off(r, 8 * o), re);
     store_parts<NP, 8>(img, kPart, op_off(64 + r, 8 * o), im);
 }
@@ -949,11 +955,19 @@ TcShape tc_shape(int32_t nrhs, int optin, int np) {
 
 }  // namespace
 
-// Room for the records of either split (sized for three parts).
+// RHS blocks of 64 per launch.  One block per launch keeps units of 32 targets
+// (the TMEM accumulators of four G sets x two unit buffers hold 2 T x 64 RHS
+// each); a launch over two blocks must halve the unit to 16 targets and measured
+// 15.4 ms on the 2^21-point ellipsoid at 128 RHS against 2 x 5.2 ms for two
+// launches of one block (G is formed once per launch: its share is small).
+constexpr int kRbLaunch = 1;
+
+// Room for the records of either split (sized for three parts), chunk by chunk.
 size_t p2p_tc_pack_bytes(int64_t n, int32_t nb, int32_t max_nrhs) {
     if (max_nrhs < 16) return 0;
     const int64_t groups = n / kSrcGroup + nb;
-    return (size_t)groups * (size_t)record_bytes((max_nrhs + 63) / 64, 3);
+    const int chunks = (max_nrhs + 64 * kRbLaunch - 1) / (64 * kRbLaunch);
+    return (size_t)chunks * (size_t)groups * (size_t)record_bytes(kRbLaunch, 3);
 }
 
 bool p2p_tc_supported(const p2p_plan* plan, int32_t nrhs) {
@@ -971,10 +985,11 @@ p2p_status p2p_tc_stage(const p2p_plan* plan, const float2* lam, int32_t nrhs, i
     if (plan->n == 0 || plan->tc_groups == 0) return P2P_OK;
     const int rb_count = (nrhs + 63) / 64;
     dim3 grid((unsigned)plan->tc_groups, (unsigned)rb_count);
+    const int64_t chunk_bytes = (int64_t)plan->tc_groups * record_bytes(kRbLaunch, np);
     // the group records are built over the SOURCE boxes
     auto pack = np == 3 ? k_tc_pack<3> : k_tc_pack<2>;
     pack<<<grid, 128, 0, s>>>(lam, ld, nrhs, plan->src_perm, plan->src_box_ptr, plan->xs_src, plan->tc_gstart,
-                              plan->nbs, rb_count, plan->tc_pack);
+                              plan->nbs, kRbLaunch, chunk_bytes, plan->tc_pack);
     P2P_CHECK_LAUNCH("p2p_apply_stage/tc_pack");
     return P2P_OK;
 }
@@ -986,7 +1001,9 @@ p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t
     P2P_TRY_CUDA(cudaGetDevice(&dev), "p2p_apply_tc");
     P2P_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "p2p_apply_tc");
     P2P_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "p2p_apply_tc");
-    const TcShape sh = tc_shape(nrhs, optin, np);
+    // one launch per chunk of kRbLaunch RHS blocks, each on its own records
+    const int chunk_rhs = 64 * kRbLaunch;
+    const TcShape sh = tc_shape(std::min(nrhs, chunk_rhs), optin, np);
     if (sh.smem > optin) {
         set_message("p2p_apply_tc: the tensor-core pipeline does not fit in shared memory");
         return P2P_ERR_UNSUPPORTED;
@@ -999,9 +1016,7 @@ p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t
     a.glist = plan->tc_glist;
     a.gcount = plan->tc_gcount;
     a.perm = plan->perm;
-    a.out = out;
     a.ld = ld;
-    a.nrhs = nrhs;
     a.rb_count = sh.rb_count;
     a.tg = sh.tg;
     a.ngrp = (plan->max_box + sh.tg - 1) / sh.tg;
@@ -1025,8 +1040,14 @@ p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t
     P2P_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem), "p2p_apply_tc");
     const int64_t units = (int64_t)a.nb * a.ngrp;
     const int grid = (int)std::min<int64_t>(units, sms);
-    kern<<<grid, kThreads, sh.smem, s>>>(a);
-    P2P_CHECK_LAUNCH("p2p_apply_tc");
+    const int64_t chunk_bytes = (int64_t)plan->tc_groups * record_bytes(kRbLaunch, np);
+    for (int c = 0; c * chunk_rhs < nrhs; ++c) {
+        a.pack = plan->tc_pack + c * chunk_bytes;
+        a.out = out + (int64_t)c * chunk_rhs;
+        a.nrhs = std::min(chunk_rhs, nrhs - c * chunk_rhs);
+        kern<<<grid, kThreads, sh.smem, s>>>(a);
+        P2P_CHECK_LAUNCH("p2p_apply_tc");
+    }
     return P2P_OK;
 }
 
