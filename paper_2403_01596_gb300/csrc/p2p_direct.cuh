@@ -49,30 +49,20 @@ struct DirectArgs {
     float k;
 };
 
-// Source s of the box's list: its coordinates and strength.
-template <bool RED>
-__device__ __forceinline__ void load_source(const DirectArgs& a, int32_t off, int s, float4& p, float2& l) {
-    if (RED) {
-        p = __ldg(a.pk_xyz + off + s);
-        l = __ldg(a.lam + off + s);
-    } else {
-        const int j = __ldg(a.nb_src + off + s);
-        p = __ldg(a.xs + j);
-        l = __ldg(a.lam + j);
-    }
-}
-
 #ifndef P2P_DIRECT_BLOCK
 #define P2P_DIRECT_BLOCK 2
 #endif
 constexpr int kBlock = P2P_DIRECT_BLOCK;  // sources per lane per block of the software pipeline
 
 // The lane's sources s0, s0 + Q, ... < ns in blocks of kBlock: while a block is
-// evaluated (pair(p, l) per source) the next block's coordinates and strengths
+// evaluated (pair(p, l, own) per source, own = s < m_end: a source of the box's
+// own cell, where r = 0 is possible) the next block's coordinates and strengths
 // are already being loaded, and for the indexed layout the list entries of the
-// block after that as well.
+// block after that as well.  The own cell's sources (the list's prefix) go
+// through the same pipeline as the rest.
 template <bool RED, typename Pair>
-__device__ __forceinline__ void sweep_blocks(const DirectArgs& a, int32_t off, int s0, int Q, int ns, Pair pair) {
+__device__ __forceinline__ void sweep_blocks(const DirectArgs& a, int32_t off, int s0, int Q, int ns, int m_end,
+                                             Pair pair) {
     if (s0 >= ns) return;
     const int stride = kBlock * Q;
     float4 p[kBlock];
@@ -112,7 +102,7 @@ __device__ __forceinline__ void sweep_blocks(const DirectArgs& a, int32_t off, i
         load_idx(base + 2 * stride);
 #pragma unroll
         for (int u = 0; u < kBlock; ++u)
-            if (base + u * Q < ns) pair(p[u], l[u]);
+            if (base + u * Q < ns) pair(p[u], l[u], base + u * Q < m_end);
 #pragma unroll
         for (int u = 0; u < kBlock; ++u) {
             p[u] = pn[u];
@@ -153,18 +143,11 @@ __device__ __forceinline__ void box_pass(const DirectArgs& a, const ItemRec& r, 
                 ax[v][0] = ay[v][0] = make_float2(0.f, 0.f);
             }
             const float2 k2 = make_float2(k, k);
-            int s = q;
-            // own cell first (r = 0 possible)
-            for (; s < m_end; s += Q) {
-                float4 p;
-                float2 l[1];
-                load_source<RED>(a, off, s, p, l[0]);
-                p2p_pair::pair_core_x2<KERN, 1, TT, true>(p, l, nx, ny, nz, ax, ay, k2);
-            }
-            // the rest in blocks of kBlock sources per lane, the next block's loads in flight
-            sweep_blocks<RED>(a, off, s, Q, ns, [&](const float4& p, const float2& l) {
+            // blocks of kBlock sources per lane, the next block's loads in flight; own cell first (r = 0 possible)
+            sweep_blocks<RED>(a, off, q, Q, ns, m_end, [&](const float4& p, const float2& l, bool own) {
                 const float2 lv[1] = {l};
-                p2p_pair::pair_core_x2<KERN, 1, TT, false>(p, lv, nx, ny, nz, ax, ay, k2);
+                if (own) p2p_pair::pair_core_x2<KERN, 1, TT, true>(p, lv, nx, ny, nz, ax, ay, k2);
+                else p2p_pair::pair_core_x2<KERN, 1, TT, false>(p, lv, nx, ny, nz, ax, ay, k2);
             });
 #pragma unroll
             for (int v = 0; v < TT / 2; ++v) {
@@ -172,16 +155,10 @@ __device__ __forceinline__ void box_pass(const DirectArgs& a, const ItemRec& r, 
                 acc[2 * v + 1][0] = make_float2(ax[v][0].y, ay[v][0].y);
             }
         } else {
-            int s = q;
-            for (; s < m_end; s += Q) {
-                float4 p;
-                float2 l[1];
-                load_source<RED>(a, off, s, p, l[0]);
-                p2p_pair::pair_core<KERN, 1, TT, true>(p, l, tx, acc, k);
-            }
-            sweep_blocks<RED>(a, off, s, Q, ns, [&](const float4& p, const float2& l) {
+            sweep_blocks<RED>(a, off, q, Q, ns, m_end, [&](const float4& p, const float2& l, bool own) {
                 const float2 lv[1] = {l};
-                p2p_pair::pair_core<KERN, 1, TT, false>(p, lv, tx, acc, k);
+                if (own) p2p_pair::pair_core<KERN, 1, TT, true>(p, lv, tx, acc, k);
+                else p2p_pair::pair_core<KERN, 1, TT, false>(p, lv, tx, acc, k);
             });
         }
     }
