@@ -1073,8 +1073,10 @@ def run_cube(args):
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak = props.multi_processor_count * MUFU_LANES_PER_SM_CLK * f_max / MUFU_PER_PAIR["helmholtz"] / 1e9
     res = {}
+    tuning = {k: v for k, v in (("chunk", args.chunk), ("warps_per_cta", args.warps),
+                                ("target_group", args.target_group), ("warp_boxes", args.warp_boxes)) if v} or None
     for layout in ("indexed", "redundant"):
-        plan = api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k, layout=layout)
+        plan = api.Plan(pts, wl.lo, wl.h, wl.ng, wl.k, layout=layout, tuning=tuning)
         out = torch.empty_like(lam)
         P = plan.pair_count()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.ext_steps)]
@@ -1099,7 +1101,7 @@ def run_cube(args):
             "steps": args.ext_steps, "warmup": 3, "ms_per_step": res["indexed"]["ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "cube_uniform_8x8x8", "n_points": wl.n, "grid": wl.ng, "k": wl.k, "pairs": P,
-                       "l2": "flushed before every apply"},
+                       "tuning": tuning or "plan defaults", "l2": "flushed before every apply"},
             "layouts": res,
             "roofline": {"bound": "alu", "kernel": "k_pair", "achieved": P / res["indexed"]["pair_kernel_ms"] / 1e6,
                          "peak": peak, "unit": "Gpair/s", "frac": res["indexed"]["pair_kernel_frac_of_mufu"]},

@@ -114,7 +114,9 @@ typedef enum {
  * chunk and warps_per_cta both zero (or a NULL tuning) the plan chooses them: 192
  * sources per item and 8 warps per block, or 256 and 6 when more than half of the
  * boxes' source lists hold 193 .. 256 sources (a 192-source item would leave each of
- * them a short tail item of the same fixed cost).
+ * them a short tail item of the same fixed cost), or 128 and 8 when the plan would
+ * have fewer than 2.5 items per resident warp (16 warps per SM; the last items
+ * would leave most warps idle).  The workspace size covers all three.
  *
  * warp_boxes selects the kernel of one-right-hand-side FP32 applies.  The staged
  * pipeline stages chunks of a box's source list in shared memory and suits boxes

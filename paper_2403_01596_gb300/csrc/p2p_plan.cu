@@ -222,6 +222,7 @@ __global__ void k_box_info(const int32_t* __restrict__ box_ptr, const int32_t* _
     atomicMax(&maxes[1], own);
     // lists just over one chunk: a full item plus a short tail item (counted for the default-tuning choice)
     if (len > chunk && 3 * len <= 4ll * chunk) atomicAdd(&maxes[2], 1);
+    atomicAdd(&maxes[3], c);  // work items in all
 }
 
 // Work-item records (unsorted) and their sort keys: larger cost (targets x
@@ -550,10 +551,11 @@ bool tuning_valid(const p2p_tuning& t) {
             t.warp_boxes == 8 || t.warp_boxes == 16 || t.warp_boxes == 32);
 }
 
-// Default launch tuning; a plan whose caller leaves chunk and warps at zero may switch to kWideTuning (see
-// p2p_plan_create).
+// Default launch tuning; a plan whose caller leaves chunk and warps at zero may switch to kWideTuning or
+// kNarrowTuning (see p2p_plan_create).
 constexpr p2p_tuning kDefaultTuning{192, 8, 32, 0};
 constexpr p2p_tuning kWideTuning{256, 6, 32, 0};
+constexpr p2p_tuning kNarrowTuning{128, 8, 32, 0};
 
 bool tuning_is_auto(const p2p_tuning* t) { return !t || (t->chunk == 0 && t->warps_per_cta == 0); }
 
@@ -603,7 +605,9 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t n_src, int32_t nbs, bool t
     memset(&L.p, 0, sizeof(L.p));
     size_t m = (size_t)(n > 0 ? n : 1), mb = (size_t)(nb > 0 ? nb : 1);
     size_t ms = (size_t)(n_src > 0 ? n_src : 1), mbs = (size_t)(nbs > 0 ? nbs : 1);
-    const size_t max_items = (size_t)(sources / t.chunk) + mb + 1;
+    // room for the items of the narrowest chunk a plan may switch to
+    const int sizing_chunk = t.chunk < kNarrowTuning.chunk ? t.chunk : kNarrowTuning.chunk;
+    const size_t max_items = (size_t)(sources / sizing_chunk) + mb + 1;
     const size_t list_bound = (size_t)sources + 3 * mb + 4;
     const bool red = layout == P2P_LAYOUT_REDUNDANT;
     L.p.status = c.take<unsigned int>(4);
@@ -991,14 +995,23 @@ p2p_status plan_create(p2p_plan** plan, const PlanInput& in, p2p_kernel kernel, 
     if (tuning_is_auto(tuning)) {
         // When most source lists hold just over one default chunk (193 .. 256 sources), every box would get a
         // full item and a short tail item with the same fixed cost; 256-source items (6 warps per block, so two
-        // blocks still fit an SM) give those boxes one item each.  The workspace sized for the default chunk
-        // covers the fewer, longer items.
-        int32_t tails = 0;
-        FAIL_CUDA(cudaMemcpyAsync(&tails, L.maxes + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
+        // blocks still fit an SM) give those boxes one item each.  When the whole plan has fewer than 2.5 items
+        // per resident warp (16 per SM), the last items of the heaviest-first list leave most warps idle;
+        // 128-source items spread it (measured on the 32 768-point cube, 8^3 boxes: 3 584 items of 192
+        // sources 60.4 us, 5 400 of 128 51.2 us, of 96 52.2 us, of 64 59.4 us).  The workspace is sized for
+        // the narrow chunk.
+        int32_t counts[2] = {0, 0};  // tails, items
+        int sms = 0, dev = 0;
+        FAIL_CUDA(cudaGetDevice(&dev), "p2p_plan_create");
+        FAIL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "p2p_plan_create");
+        FAIL_CUDA(cudaMemcpyAsync(counts, L.maxes + 2, sizeof(counts), cudaMemcpyDeviceToHost, s), "p2p_plan_create");
         FAIL_CUDA(cudaStreamSynchronize(s), "p2p_plan_create");
-        if (2ll * tails > nb) {
-            t.chunk = kWideTuning.chunk;
-            t.warps_per_cta = kWideTuning.warps_per_cta;
+        const p2p_tuning* sw = nullptr;
+        if (2ll * counts[0] > nb) sw = &kWideTuning;
+        else if (2ll * counts[1] < 5ll * 16 * sms) sw = &kNarrowTuning;
+        if (sw) {
+            t.chunk = sw->chunk;
+            t.warps_per_cta = sw->warps_per_cta;
             p->tune = t;
             FAIL_CUDA(cudaMemsetAsync(L.maxes, 0, 4 * sizeof(int32_t), s), "p2p_plan_create");
             FAIL_CUDA(box_info(), "p2p_plan_create/box_info");
