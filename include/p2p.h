@@ -124,14 +124,20 @@ typedef enum {
  * boxes (32 / warp_boxes lanes each) and reads the sources through the L1, which
  * suits sparse boxes (a few targets each), where a staged item carries too little
  * work for its fixed cost.  0: the plan decides from its mean box occupancy; -1:
- * the staged pipeline; 1 .. 32: the direct kernel with that many boxes per warp.
+ * the staged pipeline; 1 .. 32: the direct kernel with that many boxes per warp;
+ * -2 (indexed layout only, never chosen by the plan itself): the box-group
+ * kernel, in which groups of 16 consecutive target boxes stage the union of their
+ * neighbourhoods in shared memory once and every box sweeps its own neighbour
+ * boxes inside it (a plan whose largest union exceeds 8 192 sources, or of another
+ * layout, runs the staged pipeline instead and reports -1).
  * Multi-RHS applies, the symmetric layout and the batched launch always use the
  * staged pipeline. */
 typedef struct {
     int32_t chunk;         /* sources staged per work item, multiple of 32, 32..1024 (default 192) */
     int32_t warps_per_cta; /* warps per thread block of the pair kernel, 1..16 (default 8) */
     int32_t target_group;  /* targets swept per pass, multiple of 32, 32..128 (default 32) */
-    int32_t warp_boxes;    /* 0 (plan decides), -1 (staged pipeline), 1, 2, 4, 8, 16 or 32 (direct kernel) */
+    int32_t warp_boxes;    /* 0 (plan decides), -1 (staged pipeline), 1, 2, 4, 8, 16 or 32 (direct kernel),
+                              -2 (box-group kernel) */
 } p2p_tuning;
 
 typedef struct p2p_plan p2p_plan;

@@ -432,8 +432,12 @@ p2p_status p2p_abs_sums(const p2p_plan* plan, const float2* lam, int64_t ld, int
     return R == 1 ? launch_pair<1>(plan, a, s) : (R == 2 ? launch_pair<2>(plan, a, s) : launch_pair<4>(plan, a, s));
 }
 
+cudaError_t p2p_group_configure(p2p_plan* p);
+p2p_status p2p_group_launch(const p2p_plan* p, float2* out, int64_t ld, float k, cudaStream_t s);
+
 cudaError_t p2p_pair_configure(p2p_plan* plan) {
-    cudaError_t e = configure_r<1>(plan);
+    cudaError_t e = p2p_group_configure(plan);
+    if (e == cudaSuccess) e = configure_r<1>(plan);
     if (e == cudaSuccess) e = configure_r<2>(plan);
     if (e == cudaSuccess) e = configure_r<4>(plan);
     plan->direct_grid = 0;
@@ -522,6 +526,10 @@ P2P_API p2p_status p2p_apply_staged(const p2p_plan* plan, void* out, int32_t nrh
     a.ld = ld;
     a.nrhs = nrhs;
     if (adjoint) a.k = -a.k;
+    if (nrhs == 1 && plan->group_k && plan->group_grid > 0) {
+        // one right-hand side, groups of boxes staging the union of their neighbourhoods once
+        return p2p_group_launch(plan, (float2*)out, ld, a.k, s);
+    }
     if (nrhs == 1 && plan->direct_k > 0 && plan->direct_grid > 0) {
         // one right-hand side on sparse boxes: the direct kernel, one item per box, every row stored once
         DirectArgs d;

@@ -124,6 +124,20 @@ struct p2p_plan {
                             // followed by the group's 16 source coordinates
     int32_t tc_wait_polls;  // poll bound of the tensor-core pipeline's waits, -1: the default (a self-check
                             // lowers it to make the abort path run)
+    // box-group kernel (p2p_group.cu; indexed layout, one right-hand side): kGroupBoxes consecutive target boxes
+    // stage the union of their neighbour boxes once
+    int32_t group_k;        // 1: one-RHS applies run the box-group kernel
+    int32_t n_groups;       // ceil(nb / kGroupBoxes)
+    int32_t group_cap;      // largest union (sources): the kernel's coordinate and strength buffers
+    int32_t group_pos_cap;  // largest sum of a group's padded list lengths: its position buffer
+    int32_t group_grid;     // persistent grid (blocks of 8 warps)
+    int32_t* g_union;       // [n_groups * kGroupBoxes * 27] union boxes of every group, ascending
+    int32_t* g_nunion;      // [n_groups]
+    int32_t* g_order;       // [n_groups] groups, heaviest first
+    int16_t* g_pos;         // [list entries, at pk_off] every box's source list as positions in its group's buffer
+    int32_t* g_mend;        // [nb] own-box prefix of every list
+    int32_t* g_map;         // [2 nb] lane maps (full 128-target pass, last pass) of every box
+    int32_t* g_morder;      // [n_groups * kGroupBoxes] members of every group by decreasing cost
 };
 
 // Bytes of the tensor-core group records for n points in nb boxes (0 when max_nrhs < 16).
@@ -134,6 +148,12 @@ inline size_t p2p_tc_list_bound(int64_t sources, int64_t nnz, int32_t nb) {
 }
 
 namespace p2p_detail {
+
+// Target boxes per group of the box-group kernel (consecutive in Morton order; at most 32).
+#ifndef P2P_GROUP_BOXES
+#define P2P_GROUP_BOXES 16
+#endif
+constexpr int kGroupBoxes = P2P_GROUP_BOXES;
 
 // thread-local message of the last CUDA failure
 void set_cuda_error(cudaError_t e, const char* where);

@@ -22,6 +22,11 @@ void set_message(const char* msg) { snprintf(g_last_error, sizeof(g_last_error),
 
 using namespace p2p_detail;
 
+// Box-group kernel tables (p2p_group.cu).
+cudaError_t p2p_group_build(p2p_plan* p, const int32_t* nbr_ptr, const int32_t* nbr_idx, uint64_t* keys,
+                            int32_t* vals, uint64_t* keys_alt, int32_t* vals_alt, void* radix_ws, int32_t* maxes,
+                            cudaStream_t s, int32_t* cap);
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -547,8 +552,8 @@ NbrLayout nbr_layout(int32_t nb, void* work) {
 bool tuning_valid(const p2p_tuning& t) {
     return t.chunk >= 32 && t.chunk <= 1024 && t.chunk % 32 == 0 && t.warps_per_cta >= 1 && t.warps_per_cta <= 16 &&
            t.target_group >= 32 && t.target_group <= 128 && t.target_group % 32 == 0 &&
-           (t.warp_boxes == -1 || t.warp_boxes == 0 || t.warp_boxes == 1 || t.warp_boxes == 2 || t.warp_boxes == 4 ||
-            t.warp_boxes == 8 || t.warp_boxes == 16 || t.warp_boxes == 32);
+           (t.warp_boxes == -2 || t.warp_boxes == -1 || t.warp_boxes == 0 || t.warp_boxes == 1 ||
+            t.warp_boxes == 2 || t.warp_boxes == 4 || t.warp_boxes == 8 || t.warp_boxes == 16 || t.warp_boxes == 32);
 }
 
 // Default launch tuning; a plan whose caller leaves chunk and warps at zero may switch to kWideTuning or
@@ -575,6 +580,13 @@ p2p_tuning resolve_tuning(const p2p_tuning* t) {
 // against 217 us staged) and D = 16 (staged 290 us, direct 293 - 340 us), and square plates of 2^10 - 2^20
 // points at D = 1.0 - 4 (at 2^20 points: D = 4.1, eight boxes per warp 74 us, four 82 us, staged 258 us;
 // D = 1.6, sixteen 64 us; D = 1.0 - 1.1, thirty-two 39 - 47 us).
+// Largest union the box-group kernel stages (sources; 24 bytes each in shared memory; its positions are 16-bit).
+constexpr int32_t kGroupCapMax = 8192;
+
+//
+// Above that, up to D = 24, the box-group kernel (-2; indexed layout only, other layouts keep the staged
+// pipeline): the sphere at D = 16, 263 us against 292 us staged (groups of 16 boxes, 24 warps per SM); at D = 32
+// it measured 585 us against 472 staged, at D = 8 225 us against the direct kernel's 186.
 int32_t auto_warp_boxes(int64_t n, int32_t nb) {
     if (nb <= 0) return -1;
     const double d = (double)n / nb;
@@ -582,6 +594,7 @@ int32_t auto_warp_boxes(int64_t n, int32_t nb) {
     if (d <= 2.5) return 16;
     if (d <= 6.0) return 8;
     if (d <= 12.0) return 4;
+    if (d <= 24.0) return -2;
     return -1;
 }
 
@@ -617,6 +630,17 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t n_src, int32_t nbs, bool t
     L.p.box_src = c.take<int32_t>(mb);
     L.p.items = c.take<ItemRec>(max_items);
     L.p.ditems = c.take<ItemRec>(mb);
+    if (layout == P2P_LAYOUT_INDEXED && (t.warp_boxes == -2 || (t.warp_boxes == 0 && auto_warp_boxes(n, nb) == -2))) {
+        // box-group kernel tables (requested, or the plan's own choice)
+        const size_t ngr = (mb + kGroupBoxes - 1) / kGroupBoxes;
+        L.p.g_union = c.take<int32_t>(ngr * kGroupBoxes * 27);
+        L.p.g_nunion = c.take<int32_t>(ngr);
+        L.p.g_order = c.take<int32_t>(ngr);
+        L.p.g_pos = c.take<int16_t>(list_bound);
+        L.p.g_mend = c.take<int32_t>(mb);
+        L.p.g_map = c.take<int32_t>(2 * mb);
+        L.p.g_morder = c.take<int32_t>(ngr * kGroupBoxes);
+    }
     L.p.pk_off = c.take<int32_t>(mb + 1);
     L.p.nb_src = c.take<int32_t>(list_bound);
     L.p.pk_xyz = red ? c.take<float4>(list_bound) : nullptr;
@@ -1104,6 +1128,27 @@ p2p_status plan_create(p2p_plan** plan, const PlanInput& in, p2p_kernel kernel, 
         }
     } else {
         p->tune.warp_boxes = -1;
+    }
+    // box-group kernel (indexed layout): groups of consecutive target boxes staging the union of their
+    // neighbourhoods; a plan whose largest union does not fit the kernel's buffer keeps the staged pipeline
+    p->group_k = 0;
+    p->n_groups = 0;
+    p->group_cap = 0;
+    p->group_pos_cap = 0;
+    if (p->tune.warp_boxes == -2 && (layout != P2P_LAYOUT_INDEXED || nb == 0)) p->tune.warp_boxes = -1;
+    if (p->tune.warp_boxes == -2) {
+        p->n_groups = (nb + kGroupBoxes - 1) / kGroupBoxes;
+        int32_t cap[2] = {0, 0};
+        FAIL_CUDA(p2p_group_build(p, in.nbr_ptr, in.nbr_idx, L.keys, L.vals, L.keys_alt, L.vals_alt, L.radix_ws,
+                                  L.maxes, s, cap),
+                  "p2p_plan_create/groups");
+        if (cap[0] > 0 && cap[0] <= kGroupCapMax) {
+            p->group_k = 1;
+            p->group_cap = (cap[0] + 3) & ~3;
+            p->group_pos_cap = cap[1];
+        } else {
+            p->tune.warp_boxes = -1;
+        }
     }
     p->max_chunks = host[0];
     p->max_box = host[1];

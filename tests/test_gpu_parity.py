@@ -185,6 +185,40 @@ def test_direct_kernel(warp_boxes, kernel, layout):
         assert plan.async_status() == 0
 
 
+@pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
+def test_group_kernel(kernel):
+    """The box-group kernel (tuning warp_boxes = -2: groups of sixteen consecutive boxes stage the union of their
+    neighbourhoods once; every box sweeps its own neighbour boxes as segments of that buffer): dense cube (64
+    targets per box, a 4 096-source union), sparse sphere, clustered assembly (occupancy 1 - 128) and the edge
+    case of one 700-point box (several passes of 128 targets), forward and adjoint, output rows stored once
+    (the output starts as garbage); per target within 2e-6 of S_i."""
+    api = _cuda()
+    kern = oracle.HELMHOLTZ if kernel == "helmholtz" else oracle.LAPLACE
+    rng = np.random.default_rng(4)
+    p = np.concatenate([rng.random((700, 3)) * 0.1 + 0.45, rng.random((300, 3)) * 1.4 - 0.2]).astype(np.float32)
+    p[10] = p[11]
+    p[20] = p[21] = p[22]
+    edge = W.Workload("edge", p, (0, 0, 0), 0.125, 8, 9.0, 0)
+    for wl in (W.cube_dense(), _small_sphere(30000, 48, 22), _clustered(20000, 23), edge):
+        k = wl.k if kernel == "helmholtz" else 0.0
+        lam = W.strengths(wl.n, 1, 24)
+        plan = _plan(api, wl, kernel, "indexed", tuning={"warp_boxes": -2}, k=k)
+        assert plan.info["tuning"]["warp_boxes"] == -2, wl.name
+        for adjoint in (False, True):
+            out = torch.full((wl.n, 1), 5.0 - 3.0j, dtype=torch.complex64, device="cuda")
+            plan.apply(torch.from_numpy(lam).cuda(), out=out, adjoint=adjoint)
+            ref = oracle.p2p(wl.points, lam, wl.lo, wl.h, wl.ng, k, kernel=kern, adjoint=adjoint)
+            got = out.cpu().numpy()
+            err = rel_l2(got, ref).max()
+            normwise, rel = per_target(got, ref, wl, lam)
+            print(f"group kernel {wl.name} {kernel} adjoint={adjoint}: rel-L2 {err:.2e}, max |err|/S {normwise:.2e}")
+            assert err <= TOL and normwise <= 2e-6, (wl.name, adjoint, err, normwise)
+        assert plan.async_status() == 0
+    # the redundant layout keeps its own kernels
+    plan = _plan(api, W.cube_dense(), kernel, "redundant", tuning={"warp_boxes": -2})
+    assert plan.info["tuning"]["warp_boxes"] == -1
+
+
 @pytest.mark.parametrize("path", ["fp32_per_rhs", "fp32_shared"])
 @pytest.mark.parametrize("nrhs", [2, 3, 5, 8])
 def test_multi_rhs(path, nrhs):

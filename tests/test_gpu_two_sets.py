@@ -86,13 +86,18 @@ def test_two_set_structure_bit_exact(case):
         assert (self_ref < 0).sum() > 0 and (np.diff(nptr) == 0).sum() > 0  # the edge cases are present
 
 
-@pytest.mark.parametrize("layout", ["indexed", "redundant"])
+@pytest.mark.parametrize("layout", ["indexed", "redundant", "indexed_groups"])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_two_set_apply(case, layout):
+    """indexed_groups: the box-group kernel (tuning warp_boxes = -2)."""
     api = _api()
     t, s, lo, h, ng, k = CASES[case]()
     lam = W.strengths(len(s), 1, 56)
-    plan = api.TwoSetPlan(torch.from_numpy(t).cuda(), torch.from_numpy(s).cuda(), lo, h, ng, k, layout=layout)
+    tuning = {"warp_boxes": -2} if layout == "indexed_groups" else None
+    plan = api.TwoSetPlan(torch.from_numpy(t).cuda(), torch.from_numpy(s).cuda(), lo, h, ng, k,
+                          layout=layout.replace("_groups", ""), tuning=tuning)
+    if tuning:
+        assert plan.info["tuning"]["warp_boxes"] == -2
     out = torch.full((len(t),), 7.0 + 7.0j, dtype=torch.complex64, device="cuda")  # every row must be written
     plan.apply(torch.from_numpy(lam).cuda(), out=out.reshape(-1, 1))
     ref = oracle.p2p_st(t, s, lam, lo, h, ng, k)
