@@ -384,9 +384,18 @@ def _traffic_for(kernel_src_hash: str, layout: str):
     return e.get("dram_bytes_per_launch")
 
 
+def _kernel_name(warp_boxes: int) -> str:
+    """The one-RHS pair kernel a plan runs, from its tuning's warp_boxes."""
+    if warp_boxes == -2:
+        return "k_pair_group (box groups)"
+    if warp_boxes > 0:
+        return f"k_pair_direct ({warp_boxes} boxes per warp)"
+    return "k_pair (staged pipeline)"
+
+
 def _kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("p2p_apply.cu", "p2p_pair.cuh", "p2p_direct.cuh", "p2p_internal.cuh", "p2p_plan.cu"):
+    for f in ("p2p_apply.cu", "p2p_pair.cuh", "p2p_direct.cuh", "p2p_group.cu", "p2p_internal.cuh", "p2p_plan.cu"):
         h.update(open(os.path.join(ROOT, "paper_2403_01596_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -526,7 +535,8 @@ def run_ours(args):
     traffic = _traffic_for(khash, layouts[0]) if len(set(layouts)) == 1 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_pairs, "unit": "Gpair/s",
                 "frac": achieved / peak_pairs, "traffic": traffic,
-                "kernel": "k_pair_direct (D = 8) + k_pair (D = 16, 32, 64): the FP32 pair kernels the plans choose",
+                "kernel": "the FP32 pair kernels the plans choose: " + ", ".join(
+                    f"D = {d['occupancy']}: " + _kernel_name(d["tuning"].get("warp_boxes", -1)) for d in detail),
                 "peak_basis": f"MUFU: {sms} SMs x 16 lanes/clk x {f_max / 1e6:.0f} MHz / 3 MUFU per Helmholtz pair "
                               f"(sm_max_mhz {peaks['source']})",
                 "peak_at_measured_clock": (sms * 16 * clk["sm_mhz"] * 1e6 / 3 / 1e9) if clk.get("sm_mhz") else None,

@@ -283,11 +283,20 @@ __device__ __forceinline__ void member_pass(const GroupArgs& a, const float4* __
                 const float2 l[1] = {sl[j]};
                 pair_core_x2<KERN, 1, TT, true>(sx[j], l, nx, ny, nz, ax, ay, k2);
             }
-#pragma unroll 2
-            for (; s < S; s += Q) {
-                const int j = pl[s];
-                const float2 l[1] = {sl[j]};
-                pair_core_x2<KERN, 1, TT, false>(sx[j], l, nx, ny, nz, ax, ay, k2);
+            // the next source's position and data are read before this one is evaluated
+            if (s < S) {
+                int j = pl[s];
+                float4 p = sx[j];
+                float2 l[1] = {sl[j]};
+                for (; s < S; s += Q) {
+                    const int sn = s + Q;
+                    const int jn = sn < S ? pl[sn] : j;
+                    const float4 pn = sx[jn];
+                    const float2 ln = sl[jn];
+                    pair_core_x2<KERN, 1, TT, false>(p, l, nx, ny, nz, ax, ay, k2);
+                    p = pn;
+                    l[0] = ln;
+                }
             }
 #pragma unroll
             for (int v = 0; v < TT / 2; ++v) {
@@ -300,11 +309,19 @@ __device__ __forceinline__ void member_pass(const GroupArgs& a, const float4* __
                 const float2 l[1] = {sl[j]};
                 pair_core<KERN, 1, TT, true>(sx[j], l, tx, acc, k);
             }
-#pragma unroll 2
-            for (; s < S; s += Q) {
-                const int j = pl[s];
-                const float2 l[1] = {sl[j]};
-                pair_core<KERN, 1, TT, false>(sx[j], l, tx, acc, k);
+            if (s < S) {
+                int j = pl[s];
+                float4 p = sx[j];
+                float2 l[1] = {sl[j]};
+                for (; s < S; s += Q) {
+                    const int sn = s + Q;
+                    const int jn = sn < S ? pl[sn] : j;
+                    const float4 pn = sx[jn];
+                    const float2 ln = sl[jn];
+                    pair_core<KERN, 1, TT, false>(p, l, tx, acc, k);
+                    p = pn;
+                    l[0] = ln;
+                }
             }
         }
     }
