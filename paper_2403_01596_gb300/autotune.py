@@ -19,8 +19,9 @@ import os
 import statistics
 import threading
 
-# staged pipeline (warp_boxes -1) with several chunk / block shapes, and the direct kernel with 1, 2 or 4 boxes
-# per warp (one-RHS applies only; for several RHS a plan runs the staged pipeline whatever warp_boxes says)
+# staged pipeline (warp_boxes -1) with several chunk / block shapes, the direct kernel with 1 - 32 boxes per warp
+# and the box-group kernel (-2, indexed layout only) (one-RHS applies only; for several RHS a plan runs the staged
+# pipeline whatever warp_boxes says)
 DEFAULT_CANDIDATES = (
     {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": -1},
     {"chunk": 128, "warps_per_cta": 8, "target_group": 32, "warp_boxes": -1},
@@ -34,6 +35,7 @@ DEFAULT_CANDIDATES = (
     {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 8},
     {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 16},
     {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": 32},
+    {"chunk": 192, "warps_per_cta": 8, "target_group": 32, "warp_boxes": -2},
 )
 
 DEFAULT_LAYOUTS = ("indexed", "redundant", "symmetric")
@@ -56,7 +58,7 @@ def occupancy_bucket(n_points: int, num_boxes: int) -> int:
 
 
 def cache_key(gpu: str, sms: int, kernel: str, bucket: int, nrhs: int, layouts) -> str:
-    return f"v2|{gpu}|{sms}|{kernel}|d{bucket}|r{nrhs}|{'+'.join(sorted(layouts))}"
+    return f"v3|{gpu}|{sms}|{kernel}|d{bucket}|r{nrhs}|{'+'.join(sorted(layouts))}"
 
 
 def load_cache(path: str | None = None) -> dict:
@@ -128,6 +130,8 @@ def tune(structure, k: float, kernel: str = "helmholtz", nrhs: int = 1, layouts=
         for cand in candidates:
             if layout == "symmetric" and cand.get("warp_boxes", 0) > 0:
                 continue  # the symmetric layout always runs the staged pipeline
+            if layout != "indexed" and cand.get("warp_boxes", 0) == -2:
+                continue  # the box-group kernel serves the indexed layout only
             plan = Plan(structure.points, structure.lo, structure.h, structure.ng, k, kernel=kernel, layout=layout,
                         max_nrhs=nrhs, tuning=dict(cand), structure=structure)
             timings.append({"layout": layout, "tuning": dict(cand), "ms": _time_plan(plan, lam, out, reps)})

@@ -42,7 +42,11 @@ namespace {
 #define P2P_GROUP_PER_ITER 4
 #endif
 
-constexpr int kGroupWarps = 8;   // warps of the apply kernel's blocks
+#ifndef P2P_GROUP_WARPS
+#define P2P_GROUP_WARPS 8
+#endif
+
+constexpr int kGroupWarps = P2P_GROUP_WARPS;  // warps of the apply kernel's blocks
 constexpr int kBuildWarps = 4;
 constexpr int kUnionMax = kGroupBoxes * 27;  // union entries of a group at most
 constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }

@@ -19,9 +19,13 @@ def test_autotune_picks_caches_and_is_correct(tmp_path):
     st = api.BoxStructure(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng)
     first = autotune.tune(st, wl.k, reps=3, path=cache)
     assert not first["cached"]
-    # every (layout, candidate) but the direct-kernel candidates of the symmetric layout, which runs staged
+    # every (layout, candidate) but the direct-kernel candidates of the symmetric layout, which runs staged, and
+    # the box-group candidates of the layouts other than indexed
     direct = sum(1 for c in autotune.DEFAULT_CANDIDATES if c.get("warp_boxes", 0) > 0)
-    assert len(first["all"]) == len(autotune.DEFAULT_LAYOUTS) * len(autotune.DEFAULT_CANDIDATES) - direct
+    group = sum(1 for c in autotune.DEFAULT_CANDIDATES if c.get("warp_boxes", 0) == -2)
+    others = sum(1 for lay in autotune.DEFAULT_LAYOUTS if lay != "indexed")
+    assert len(first["all"]) == (len(autotune.DEFAULT_LAYOUTS) * len(autotune.DEFAULT_CANDIDATES) - direct
+                                 - others * group)
     assert abs(first["ms"] - min(t[4] for t in first["all"])) <= 1e-5  # "all" keeps 5 decimals
     again = autotune.tune(st, wl.k, reps=3, path=cache)
     assert again["cached"] and again["layout"] == first["layout"] and again["tuning"] == first["tuning"]
