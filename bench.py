@@ -394,9 +394,15 @@ def _kernel_name(warp_boxes: int) -> str:
 
 
 def _kernel_hash() -> str:
+    """Hash of the pair kernels' sources with comments and blank lines removed (a comment edit keeps the DRAM
+    traffic record valid; any code change drops it)."""
+    import re
     h = hashlib.sha256()
     for f in ("p2p_apply.cu", "p2p_pair.cuh", "p2p_direct.cuh", "p2p_group.cu", "p2p_internal.cuh", "p2p_plan.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2403_01596_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2403_01596_gb300", "csrc", f), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("\n".join(line.rstrip() for line in src.splitlines() if line.strip()).encode())
     return h.hexdigest()
 
 
