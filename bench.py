@@ -909,7 +909,7 @@ def run_tree_sweep(args):
     CT = 15 tree level (4 points per box on average: N = 4 x boxes) raised or lowered by i in {-3 .. 3}, i.e. a
     plate grid of 2^(L - 1 + i) boxes per side, D = 4 / 4^i points per box.  Laplace kernel (the paper applies a
     potential kernel).  Per configuration: kernel-only time of the indexed layout (Sec. 3.2), the box-level
-    redundant layout, the paper's per-target repetition layout (Sec. 3.3) and the direct kernel, plus the
+    redundant layout, the paper's per-target repetition layout (Sec. 3.3), the direct and box-group kernels and the plan's own choice, plus the
     repetition layout's per-apply strength repack; the speedup of repetition over indexing, X = T_indexed /
     T_repetition, next to the paper's kernel model (eq. 28), X = 55.3 lambda t / (N D), whose lambda is fitted
     by least squares in log space over the measured points."""
@@ -943,6 +943,7 @@ def run_tree_sweep(args):
                                           ("direct8", "indexed", {"warp_boxes": 8}),
                                           ("direct16", "indexed", {"warp_boxes": 16}),
                                           ("direct32", "indexed", {"warp_boxes": 32}),
+                                          ("group", "indexed", {"warp_boxes": -2}),
                                           ("auto", "indexed", None)):
                 try:
                     plan = api.Plan(pts, (0.0, 0.0, 0.0), 1.0 / ng, ng, 0.0, kernel="laplace", layout=layout,
