@@ -888,7 +888,7 @@ def run_batched(args):
             "config": {"workload": "batched_cylinder_plates", "n_points": [g.n for g in geos],
                        "grids": [g.ng for g in geos], "max_occupancy": [g.meta["max_occupancy"] for g in geos],
                        "nrhs": nrhs, "pairs_per_rhs": pairs, "work_items": batch.info["work_items"],
-                       "grid_ctas": batch.info["grid"], "plan_s": t_plan},
+                       "grid_ctas": batch.info["grid"], "setup_s": t_plan, "setup": "host generation of the 40 M points and strengths, copies, binning, neighbour lists and plans"},
             "separate_applies_ms": sep, "speedup_vs_separate_applies": sep / med,
             "rel_l2_vs_fp64_per_geometry": errs,
             "cpu_baseline": {"value": cpu_pairs / cpu_s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
