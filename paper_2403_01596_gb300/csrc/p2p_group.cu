@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
                   const int32_t* __restrict__ src_box_ptr, const int32_t* __restrict__ box_src,
                   const int32_t* __restrict__ pk_off, int32_t nb, int32_t n_groups, int32_t* __restrict__ g_union,
                   int32_t* __restrict__ g_nunion, int16_t* __restrict__ g_pos, int32_t* __restrict__ g_mend,
-                  int32_t* __restrict__ g_map, int32_t* __restrict__ g_morder, uint64_t* __restrict__ keys,
-                  int32_t* __restrict__ vals, int32_t* __restrict__ maxes) {
+                  int32_t* __restrict__ g_map, int32_t* __restrict__ g_morder, int4* __restrict__ g_copy,
+                  uint64_t* __restrict__ keys, int32_t* __restrict__ vals, int32_t* __restrict__ maxes) {
     __shared__ int32_t buf_all[kBuildWarps][kSortSlots];
     __shared__ int32_t off_all[kBuildWarps][kUnionMax + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -154,6 +154,9 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
         atomicMax(&maxes[1], pk_off[b1] - pk_off[b0]);
     }
     __syncwarp();
+    // the copies that stage the union: source start, buffer offset and length of every union box
+    for (int i = lane; i < nu; i += 32)
+        g_copy[g * kUnionMax + i] = make_int4(src_box_ptr[buf[i]], uoff[i], uoff[i + 1] - uoff[i], 0);
     // members: their lists (own box first, then the others ascending, as the plan's source lists) as buffer
     // positions; lane = entry of the member's neighbour list, moved to its place in that order
     int64_t cost = 0;
@@ -226,6 +229,7 @@ struct GroupArgs {
     const int32_t* g_mend;  // own-box prefix of every list
     const int32_t* g_map;   // lane maps of a full pass and of the last pass of every box
     const int32_t* g_morder;  // members of every group by decreasing cost
+    const int4* g_copy;     // per group and union box: source start, buffer offset, length
     const int32_t* pk_off;
     const int32_t* box_ptr;
     const int32_t* box_src;
@@ -389,12 +393,13 @@ __device__ __forceinline__ void sweep_member(const GroupArgs& a, const float4* s
 }
 
 // Shared memory of a block: coordinates and strengths of the union (cap entries), the members' positions
-// (pos_cap 16-bit entries), the union offsets, the member counter and the warps' slice-reduction buffers.
+// (pos_cap 16-bit entries), the next group's union copies, the member counter and the warps' slice-reduction
+// buffers.
 struct GroupSmem {
     float4* sx;
     float2* sl;
     int16_t* pos;
-    int32_t* uoff;
+    int4* ents;
     int32_t* next;
     float2* red;
 };
@@ -402,7 +407,7 @@ struct GroupSmem {
 __host__ __device__ inline size_t pos_bytes(int pos_cap) { return ((size_t)pos_cap * 2 + 15) / 16 * 16; }
 
 __host__ __device__ inline size_t group_smem_bytes(int cap, int pos_cap) {
-    return (size_t)cap * 24 + pos_bytes(pos_cap) + 4 * (kUnionMax + 4) + (size_t)kGroupWarps * kMaxTT * 32 * 8;
+    return (size_t)cap * 24 + pos_bytes(pos_cap) + 16 * kUnionMax + 16 + (size_t)kGroupWarps * kMaxTT * 32 * 8;
 }
 
 __device__ __forceinline__ GroupSmem group_smem(unsigned char* smem, int cap, int pos_cap) {
@@ -411,10 +416,18 @@ __device__ __forceinline__ GroupSmem group_smem(unsigned char* smem, int cap, in
     m.sl = reinterpret_cast<float2*>(smem + (size_t)cap * 16);
     m.pos = reinterpret_cast<int16_t*>(smem + (size_t)cap * 24);
     unsigned char* q = smem + (size_t)cap * 24 + pos_bytes(pos_cap);
-    m.uoff = reinterpret_cast<int32_t*>(q);
-    m.next = m.uoff + kUnionMax + 1;
-    m.red = reinterpret_cast<float2*>(q + 4 * (kUnionMax + 4));
+    m.ents = reinterpret_cast<int4*>(q);
+    m.next = reinterpret_cast<int32_t*>(q + 16 * kUnionMax);
+    m.red = reinterpret_cast<float2*>(q + 16 * kUnionMax + 16);
     return m;
+}
+
+// Group g's copy list (one int4 per union box) into shared memory, as its own cp.async group.
+__device__ __forceinline__ void prefetch_copies(const GroupArgs& a, int32_t g, int4* ents) {
+    const int nu = __ldg(a.g_nunion + g);
+    const int4* src = a.g_copy + (int64_t)g * kUnionMax;
+    for (int i = threadIdx.x; i < nu; i += kGroupWarps * 32) cp_async16(ents + i, src + i);
+    cp_async_commit();
 }
 
 // Block = one group at a time: warp w takes the group's w-th costliest member, then further members from a
@@ -425,66 +438,39 @@ __global__ void __launch_bounds__(kGroupWarps * 32, P2P_GROUP_MIN_BLOCKS) k_pair
     const GroupSmem sm = group_smem(smem, a.cap, a.pos_cap);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* red = sm.red + warp * kMaxTT * 32;
+    // the first group's union copies, read ahead into shared memory like every later group's
+    if (blockIdx.x < a.n_groups) prefetch_copies(a, __ldg(a.order + blockIdx.x), sm.ents);
     for (int64_t gi = blockIdx.x; gi < a.n_groups; gi += gridDim.x) {
         const int32_t g = __ldg(a.order + gi);
         const int nu = __ldg(a.g_nunion + g);
-        const int32_t* U = a.g_union + (int64_t)g * kUnionMax;
         const int32_t b0 = g * kGroupBoxes;
         const int nm = min(a.nb - b0, kGroupBoxes);
         const int32_t* order = a.g_morder + (int64_t)g * kGroupBoxes;
         const int32_t pos0 = __ldg(a.pk_off + b0), npos = __ldg(a.pk_off + b0 + nm) - pos0;
+        // this group's copy list has arrived, and every warp has finished the previous group
+        cp_async_wait<0>();
+        __syncthreads();
+        // the union: one warp per union box, its sources contiguous in the buffer; the members' position lists
+        // contiguous from the group's first list (every list padded to 4 entries, so 8-byte copies)
+        for (int u = warp; u < nu; u += kGroupWarps) {
+            const int4 c = sm.ents[u];
+            for (int e = lane; e < c.z; e += 32) {
+                cp_async16(sm.sx + c.y + e, a.xs + c.x + e);
+                cp_async8(sm.sl + c.y + e, a.lam + c.x + e);
+            }
+        }
+        for (int e = threadIdx.x; e < npos / 4; e += kGroupWarps * 32)
+            cp_async8(sm.pos + 4 * e, a.g_pos + pos0 + 4 * e);
+        cp_async_commit();
         // this warp's first member, loaded while the union is staged
         Member m;
         const bool has = warp < nm;
         if (has) load_member(a, b0 + __ldg(order + warp), lane, m);
         if (threadIdx.x == 0) *sm.next = kGroupWarps;
-        // buffer offsets of the union boxes (warp 0)
-        if (warp == 0) {
-            constexpr int kPer = (kUnionMax + 31) / 32;
-            int sz[kPer];
-            int tot = 0;
-#pragma unroll
-            for (int u = 0; u < kPer; ++u) {
-                const int i = lane * kPer + u;
-                sz[u] = 0;
-                if (i < nu) {
-                    const int32_t c = __ldg(U + i);
-                    sz[u] = __ldg(a.src_box_ptr + c + 1) - __ldg(a.src_box_ptr + c);
-                }
-                tot += sz[u];
-            }
-            int run = tot;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(P2P_FULL_MASK, run, o);
-                if (lane >= o) run += y;
-            }
-            int acc = run - tot;
-#pragma unroll
-            for (int u = 0; u < kPer; ++u) {
-                const int i = lane * kPer + u;
-                if (i <= nu) sm.uoff[i] = acc;
-                acc += sz[u];
-            }
-        }
-        // the members' position lists: contiguous from the group's first list (every list padded to 4 entries,
-        // so 8-byte copies)
-        for (int e = threadIdx.x; e < npos / 4; e += kGroupWarps * 32)
-            cp_async8(sm.pos + 4 * e, a.g_pos + pos0 + 4 * e);
-        __syncthreads();
-        // the union: one warp per union box, its sources contiguous in the buffer
-        for (int u = warp; u < nu; u += kGroupWarps) {
-            const int32_t c = __ldg(U + u);
-            const int32_t base = __ldg(a.src_box_ptr + c);
-            const int dst = sm.uoff[u], len = sm.uoff[u + 1] - dst;
-            for (int e = lane; e < len; e += 32) {
-                cp_async16(sm.sx + dst + e, a.xs + base + e);
-                cp_async8(sm.sl + dst + e, a.lam + base + e);
-            }
-        }
-        cp_async_commit();
         cp_async_wait<0>();
         __syncthreads();
+        // the next group's copy list, in flight while this group is swept
+        if (gi + gridDim.x < a.n_groups) prefetch_copies(a, __ldg(a.order + gi + gridDim.x), sm.ents);
         if (has) {
             sweep_member<KERN>(a, sm.sx, sm.sl, sm.pos, pos0, red, m, lane);
             while (true) {
@@ -496,7 +482,6 @@ __global__ void __launch_bounds__(kGroupWarps * 32, P2P_GROUP_MIN_BLOCKS) k_pair
                 sweep_member<KERN>(a, sm.sx, sm.sl, sm.pos, pos0, red, m, lane);
             }
         }
-        __syncthreads();  // the buffers are restaged for the next group
     }
 }
 
@@ -515,7 +500,8 @@ cudaError_t p2p_group_build(p2p_plan* p, const int32_t* nbr_ptr, const int32_t* 
     if (e != cudaSuccess) return e;
     k_group_build<<<(unsigned)((ng + kBuildWarps - 1) / kBuildWarps), kBuildWarps * 32, 0, s>>>(
         nbr_ptr, nbr_idx, p->two_sets ? p->nbr_self : nullptr, p->box_ptr, p->src_box_ptr, p->box_src, p->pk_off,
-        p->nb, ng, p->g_union, p->g_nunion, p->g_pos, p->g_mend, p->g_map, p->g_morder, keys, vals, maxes);
+        p->nb, ng, p->g_union, p->g_nunion, p->g_pos, p->g_mend, p->g_map, p->g_morder, p->g_copy, keys, vals,
+        maxes);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     bool in_alt = false;
@@ -561,6 +547,7 @@ p2p_status p2p_group_launch(const p2p_plan* p, float2* out, int64_t ld, float k,
     a.g_mend = p->g_mend;
     a.g_map = p->g_map;
     a.g_morder = p->g_morder;
+    a.g_copy = p->g_copy;
     a.pk_off = p->pk_off;
     a.box_ptr = p->box_ptr;
     a.box_src = p->box_src;

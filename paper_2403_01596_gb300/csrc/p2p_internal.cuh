@@ -138,6 +138,7 @@ struct p2p_plan {
     int32_t* g_mend;        // [nb] own-box prefix of every list
     int32_t* g_map;         // [2 nb] lane maps (full 128-target pass, last pass) of every box
     int32_t* g_morder;      // [n_groups * kGroupBoxes] members of every group by decreasing cost
+    int4* g_copy;           // [n_groups * kGroupBoxes * 27] union copies: source start, buffer offset, length
 };
 
 // Bytes of the tensor-core group records for n points in nb boxes (0 when max_nrhs < 16).

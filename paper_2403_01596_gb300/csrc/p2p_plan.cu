@@ -642,6 +642,7 @@ PlanLayout plan_layout(int64_t n, int32_t nb, int64_t n_src, int32_t nbs, bool t
         L.p.g_mend = c.take<int32_t>(mb);
         L.p.g_map = c.take<int32_t>(2 * mb);
         L.p.g_morder = c.take<int32_t>(ngr * kGroupBoxes);
+        L.p.g_copy = c.take<int4>(ngr * kGroupBoxes * 27);
     }
     L.p.pk_off = c.take<int32_t>(mb + 1);
     L.p.nb_src = c.take<int32_t>(list_bound);
