@@ -18,13 +18,19 @@
 // buffer positions, and the members are ranked by cost.  Groups are ordered by
 // cost (targets x sources), heaviest first.
 //
-// Apply (k_pair_group, 8 warps per block, persistent): per group, every warp
+// Apply (k_pair_group, 8 warps per block, persistent): per group, the warps
+// copy the union boxes' coordinates and staged strengths and the members'
+// position lists (cp.async) following the group's copy list, which was read
+// into shared memory while the previous group was swept; meanwhile every warp
 // loads its first member's lane map (built at plan time), targets and output
-// rows, the warps copy the union boxes' coordinates and staged strengths and the
-// members' position lists (cp.async), and each warp sweeps the group's costliest
-// member not yet taken (the first eight one each, the rest from a shared
-// counter): TT targets per lane, Q source slices, the slice partials summed
-// through shared memory.
+// rows; then each warp sweeps the group's costliest member not yet taken (the
+// first eight one each, the rest from a shared counter): TT targets per lane, Q
+// source slices, the next source read ahead, the slice partials summed through
+// shared memory.
+//
+// Build parameters (measured on the sphere at 16 points per box): groups of 16
+// boxes, 8 warps per block, 80 registers (3 blocks per SM); groups of 24 or 32,
+// blocks of 4 warps, 64 registers or two buffers per block measured slower.
 #include <algorithm>
 
 #include "p2p_pair.cuh"
