@@ -217,6 +217,11 @@ def test_group_kernel(kernel):
     # the redundant layout keeps its own kernels
     plan = _plan(api, W.cube_dense(), kernel, "redundant", tuning={"warp_boxes": -2})
     assert plan.info["tuning"]["warp_boxes"] == -1
+    # a plan left to choose takes the box-group kernel at 12 < D <= 24 (here ~18 points per box)
+    p18 = W.unit_sphere(20000, 4)
+    wl18 = W.Workload("sphere18", p18, (-1.0, -1.0, -1.0), 2.0 / 16, 16, 2 * np.pi / (4 * 2.0 / 16), 4)
+    plan = _plan(api, wl18, kernel, "indexed", k=wl18.k if kernel == "helmholtz" else 0.0)
+    assert plan.info["tuning"]["warp_boxes"] == -2
 
 
 @pytest.mark.parametrize("path", ["fp32_per_rhs", "fp32_shared"])
