@@ -217,6 +217,14 @@ def test_group_kernel(kernel):
     # the redundant layout keeps its own kernels
     plan = _plan(api, W.cube_dense(), kernel, "redundant", tuning={"warp_boxes": -2})
     assert plan.info["tuning"]["warp_boxes"] == -1
+    # a union beyond the kernel's 8 192-source buffer: the plan reports and runs the staged pipeline
+    dense = W.Workload("dense4", W.uniform_cube(9600, 7), (0.0, 0.0, 0.0), 0.25, 4, 2 * np.pi * 2, 7)
+    lamd = W.strengths(dense.n, 1, 7)
+    kd = dense.k if kernel == "helmholtz" else 0.0
+    plan = _plan(api, dense, kernel, "indexed", tuning={"warp_boxes": -2}, k=kd)
+    assert plan.info["tuning"]["warp_boxes"] == -1
+    out = plan.apply(torch.from_numpy(lamd).cuda()).cpu().numpy()
+    assert rel_l2(out, oracle.p2p(dense.points, lamd, dense.lo, dense.h, dense.ng, kd, kernel=kern)).max() <= TOL
     # a plan left to choose takes the box-group kernel at 12 < D <= 24 (here ~18 points per box)
     p18 = W.unit_sphere(20000, 4)
     wl18 = W.Workload("sphere18", p18, (-1.0, -1.0, -1.0), 2.0 / 16, 16, 2 * np.pi / (4 * 2.0 / 16), 4)
