@@ -218,7 +218,8 @@ def test_group_kernel(kernel):
     plan = _plan(api, W.cube_dense(), kernel, "redundant", tuning={"warp_boxes": -2})
     assert plan.info["tuning"]["warp_boxes"] == -1
     # a union beyond the kernel's 8 192-source buffer: the plan reports and runs the staged pipeline
-    dense = W.Workload("dense4", W.uniform_cube(9600, 7), (0.0, 0.0, 0.0), 0.25, 4, 2 * np.pi * 2, 7)
+    # (4^3 boxes of ~256 points: a group of 16 boxes has a union of at least 36 boxes, ~9 200 sources)
+    dense = W.Workload("dense4", W.uniform_cube(16384, 7), (0.0, 0.0, 0.0), 0.25, 4, 2 * np.pi * 2, 7)
     lamd = W.strengths(dense.n, 1, 7)
     kd = dense.k if kernel == "helmholtz" else 0.0
     plan = _plan(api, dense, kernel, "indexed", tuning={"warp_boxes": -2}, k=kd)
