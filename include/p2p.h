@@ -123,9 +123,11 @@ typedef enum {
  * of many targets; the direct kernel gives each warp 1, 2, 4, 8, 16 or 32 whole
  * boxes (32 / warp_boxes lanes each) and reads the sources through the L1, which
  * suits sparse boxes (a few targets each), where a staged item carries too little
- * work for its fixed cost.  0: the plan decides from its mean box occupancy; -1:
- * the staged pipeline; 1 .. 32: the direct kernel with that many boxes per warp;
- * -2 (indexed layout only, never chosen by the plan itself): the box-group
+ * work for its fixed cost.  0: the plan decides from its mean box occupancy D (the
+ * direct kernel with 32, 16, 8 or 4 boxes per warp up to D = 1.3, 2.5, 6 and 12,
+ * the box-group kernel for 12 < D <= 24 on the indexed layout, the staged pipeline
+ * above); -1: the staged pipeline; 1 .. 32: the direct kernel with that many boxes
+ * per warp; -2 (indexed layout only): the box-group
  * kernel, in which groups of 16 consecutive target boxes stage the union of their
  * neighbourhoods in shared memory once and every box sweeps its own neighbour
  * boxes inside it (a plan whose largest union exceeds 8 192 sources, or of another
