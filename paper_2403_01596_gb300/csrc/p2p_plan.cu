@@ -242,11 +242,15 @@ __global__ void k_item_records(const int32_t* __restrict__ n_chunks, const int32
     const int32_t c = n_chunks[b], o = item_off[b];
     const int32_t tb = box_ptr[b], nt = box_ptr[b + 1] - tb, S = list_len[b];
     const int32_t last = nt - ((nt - 1) / tg) * tg;  // targets of the last target group
+    // the list in c near-equal items (multiples of 4 entries but the last, at most chunk each) rather than c - 1
+    // full items and a short tail
+    int32_t L = c > 1 ? (((S + c - 1) / c + 3) & ~3) : chunk;
+    if ((c - 1) * L >= S) L = chunk;
     for (int32_t i = 0; i < c; ++i) {
-        const int32_t s0 = i * chunk;
+        const int32_t s0 = i * L;
         ItemRec r;
         r.src_off = pk_off[b] + s0;
-        r.ns = min(chunk, S - s0);
+        r.ns = min(L, S - s0);
         r.tb = tb;
         r.nt = nt;
         // the own cell's sources lead the list; in a one-set plan they are the box's targets themselves
