@@ -440,10 +440,16 @@ __device__ __forceinline__ void set_abort(const TcArgs& a, const TcSmem& sm) {
     atomicOr(a.status, P2P_DEV_TIMEOUT | P2P_DEV_TC_FAULTED);
 }
 
-// Unit u of the round-robin sequence: target box, first target, target count (0: empty unit).
+// Unit u of the round-robin sequence: target box, first target, target count (0: empty unit).  Units run box
+// by box in Morton order, a box's ngrp target groups next to each other (CTAs serving neighbouring units share
+// records in L2).  When the grid is a multiple of ngrp, each round of the grid covers whole boxes and a CTA
+// would take the same group of every box it serves -- the CTAs of the first group carrying most of the work --
+// so round k rotates the groups of its boxes by k.
 __device__ __forceinline__ void unit_of(const TcArgs& a, int64_t u, int& b, int& t0, int& nt) {
     b = (int)(u / a.ngrp);
-    t0 = (int)(u - (int64_t)b * a.ngrp) * a.tg;
+    int j = (int)(u - (int64_t)b * a.ngrp);
+    if (gridDim.x % (unsigned)a.ngrp == 0) j = (int)((j + u / gridDim.x) % a.ngrp);
+    t0 = j * a.tg;
     const int n_b = a.box_ptr[b + 1] - a.box_ptr[b];
     nt = max(0, min(a.tg, n_b - t0));
 }

@@ -163,6 +163,29 @@ def test_tc_full_size_ellipsoid_sampled():
     assert rel_l2(out[targets], ref).max() <= TOL
 
 
+@pytest.mark.parametrize("path", TC_PATHS)
+def test_tc_two_target_groups_per_box(path):
+    """Boxes of 33 - 64 targets (two units of up to 32 targets each) on a grid of one CTA per SM: every round of
+    the grid covers whole boxes, and the units' target groups rotate between rounds.  The 2^20-point sphere at
+    16 points per box (max 50): sampled targets against the oracle, all targets against the FP32 path."""
+    api = _api()
+    wl = W.sphere_density(16)
+    nrhs = 64
+    lam = W.strengths(wl.n, nrhs, 12)
+    plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, wl.k, max_nrhs=nrhs)
+    assert 32 < int(torch.diff(plan.structure.box_ptr.long()).max().item()) <= 64
+    lam_d = torch.from_numpy(lam).cuda()
+    out = plan.apply(lam_d, path=path).cpu().numpy()
+    assert plan.async_status() == 0
+    fp32 = plan.apply(lam_d, path="fp32_shared").cpu().numpy()
+    assert rel_l2(out, fp32).max() <= TOL
+    targets = np.random.default_rng(12).choice(wl.n, 300, replace=False)
+    ref = oracle.p2p_targets(wl.points, lam, targets, wl.lo, wl.h, wl.ng, wl.k)
+    err = rel_l2(out[targets], ref)
+    print(f"{path} two target groups per box: rel-L2 max {err.max():.3e}")
+    assert err.max() <= TOL
+
+
 @pytest.mark.parametrize("kernel", ["helmholtz", "laplace"])
 def test_tc_six_products_meet_fp32_bound(kernel):
     """Per target and RHS, |err| / S_i of the six-product path stays under the FP32 path's 2^-20 (the
