@@ -36,8 +36,10 @@
 //                shared memory and writes out[perm[t]]
 // (with P2P_TC_SETS = 2: two producers, two sets of eight warps, entries taken in pairs)
 // Four independent issue chains (one per set) keep the tensor core fed with the
-// small (N = 2T) MMAs; two TMEM buffers alternate between a CTA's units so the
-// epilogue of one unit overlaps the MMAs of the next.
+// small (N = 2T) MMAs.  With the hi/lo split (units of up to 32 targets) two TMEM
+// buffers alternate between a CTA's units so the epilogue of one unit overlaps
+// the MMAs of the next; the three-part split takes units of up to 64 targets in
+// one buffer.
 //
 // Every wait is bounded: a wait that runs out sets the plan's status word and an
 // abort flag; every role then stops (the epilogue warps decide together through
@@ -61,7 +63,7 @@ constexpr int kSrcGroup = 16;          // sources per stage (MMA K)
 constexpr int kPart = 4096;            // one BF16 image of a 128 x 16 A operand
 constexpr int kImage = 2 * kPart;      // hi + lo images (the operand self-check)
 constexpr int kLbo = 128, kSbo = 256;  // core-matrix strides (K direction, 8-row groups)
-constexpr int kSetCols = 256;          // TMEM columns of one unit buffer (an accumulator per G set)
+constexpr int kSetCols = 256;          // TMEM columns of a unit buffer of 32-target units (an accumulator per set)
 // G sets (independent producer -> G -> MMA chains; 2 or 4, the group lists are
 // padded to multiples of 4).  Four sets of four warps measured twice as fast as
 // two sets of eight (units of up to 64 targets, half the stages).
@@ -381,6 +383,7 @@ struct TcArgs {
     int32_t slots;                 // pipeline slots per G set
     int32_t slot_bytes;
     int32_t np;                    // BF16 parts per operand: 2 (hi, lo) or 3 (hi, mid, lo)
+    int32_t nbuf;                  // unit buffers in TMEM (512 / (kSets x 2 tg x rb_count)): 2, or 1 at 64 targets
     float k;
     unsigned int* status;
     uint32_t wait_limit;           // polls of every pipeline wait (kWaitLimit unless a self-check lowers it)
@@ -663,9 +666,14 @@ __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int se
     const uint32_t wlim = LIMITED ? a.wait_limit : kWaitLimit;
     const int b_off = slot_b_off(a.rb_count, a.tg, NP), b_half = slot_b_half(a.tg);
     const int meta_off = slot_meta_off(a.rb_count, a.tg, NP);
-    const uint32_t acc_cols = (uint32_t)(a.rb_count * 2 * a.tg);
-    Ring r{0, 0u};
-    uint32_t unit = 0;
+    const uint32_t acc_cols = (uint32_t)(a.rb_count * 2 * a.tg), bufcols = 512u / (uint32_t)a.nbuf;
+    // The issuing thread is on every stage's critical path: per stage it only adds the slot's offset to
+    // descriptors and accumulator addresses prepared here (a descriptor's start address is its low 14 bits, in
+    // 16-byte units, and shared memory stays below 2^18 bytes, so the sum never carries out of the field).
+    const uint32_t set_base = smem_u32(sm.slots + (size_t)set * a.slots * a.slot_bytes);
+    const uint64_t da_set = smem_desc(set_base), db_set = smem_desc(set_base + (uint32_t)b_off);
+    const uint32_t d_set = tmem + (uint32_t)set * acc_cols;
+    Ring r{0, 0u}, ab{0, 0u};  // pipeline slot; accumulator buffer of the current unit
     bool acc_started = false, issued = false;
     while (true) {
         const int idx = set * a.slots + r.slot;
@@ -676,10 +684,10 @@ __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int se
         }
         const int4 m = *reinterpret_cast<const int4*>(base + meta_off);
         if (m.y & kDone) break;
-        const uint32_t ub = unit & 1u;
+        const uint32_t ub = (uint32_t)ab.slot;
         if (m.y & kFirst) {
-            // the epilogue has released this accumulator buffer (unit - 2)
-            if (!mbar_wait(&sm.acc_empty[ub], ((unit >> 1) & 1u) ^ 1u, abort, wlim)) {
+            // the epilogue has released this accumulator buffer (unit - nbuf)
+            if (!mbar_wait(&sm.acc_empty[ub], ab.phase ^ 1u, abort, wlim)) {
                 if (!*abort) set_abort(a, sm);
                 break;
             }
@@ -693,13 +701,13 @@ __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int se
         if (m.x >= 0) {
             const int T = (m.z + 7) & ~7;
             const uint32_t idesc = idesc_bf16_f32(2 * T);
-            const uint32_t sbase = smem_u32(base);
             // descriptors address 16-byte units: part p of an operand is p * bytes-per-part / 16 further
-            const uint64_t db0 = smem_desc(sbase + (uint32_t)b_off);
+            const uint64_t slot16 = (uint64_t)(((uint32_t)r.slot * (uint32_t)a.slot_bytes) >> 4);
+            const uint64_t db0 = db_set + slot16;
             const uint64_t db_step = (uint64_t)(b_half >> 4);
-            const uint32_t d0 = tmem + ub * kSetCols + (uint32_t)set * acc_cols;
+            const uint32_t d0 = d_set + ub * bufcols;
             for (int rb = 0; rb < a.rb_count; ++rb) {
-                const uint64_t da0 = smem_desc(sbase + (uint32_t)(rb * NP * kPart));
+                const uint64_t da0 = da_set + slot16 + (uint64_t)((rb * NP * kPart) >> 4);
                 const uint64_t da_step = (uint64_t)(kPart >> 4);
                 const uint32_t d = d0 + (uint32_t)(rb * 2 * a.tg);
                 // every product of parts p (of lambda) and q (of G) with p + q < NP: 3 MMAs for hi / lo,
@@ -719,7 +727,7 @@ __device__ void run_mma(const TcArgs& a, const TcSmem& sm, uint32_t tmem, int se
         issued = true;
         if (m.y & kLast) {
             mma_commit(&sm.acc_full[ub]);
-            ++unit;
+            ab.advance(a.nbuf);
         }
         r.advance(a.slots);
     }
@@ -742,7 +750,8 @@ __device__ void run_epilogue(const TcArgs& a, const TcSmem& sm, uint32_t tmem, i
     const int m = q * 32 + lane;  // accumulator row
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
     const uint32_t acc_cols = (uint32_t)(a.rb_count * 2 * a.tg);
-    uint32_t k = 0;
+    const uint32_t bufcols = 512u / (uint32_t)a.nbuf;
+    Ring eb{0, 0u};  // accumulator buffer of the next unit
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
         int b, t0, nt;
         unit_of(a, u, b, t0, nt);
@@ -753,8 +762,8 @@ __device__ void run_epilogue(const TcArgs& a, const TcSmem& sm, uint32_t tmem, i
         const int used = min(kSets, a.gcount[b]);
         const int T = (nt + 7) & ~7;
         const int tb = a.box_ptr[b] + t0;
-        const uint32_t ub = k & 1u, par = (k >> 1) & 1u;
-        ++k;
+        const uint32_t ub = (uint32_t)eb.slot, par = eb.phase;
+        eb.advance(a.nbuf);
         const bool ok = mbar_wait(&sm.acc_full[ub], par, abort, wlim);
         // the 128 threads leave together (they meet at named barriers below)
         if (epi_any(!ok)) {
@@ -771,7 +780,7 @@ __device__ void run_epilogue(const TcArgs& a, const TcSmem& sm, uint32_t tmem, i
 #pragma unroll
                     for (int j = 0; j < 8; ++j) prow[j] = c0 + j < nt ? a.perm[tb + c0 + j] : 0;
                 }
-                const uint32_t col = lane_addr + ub * kSetCols + (uint32_t)(rb * 2 * a.tg + c0);
+                const uint32_t col = lane_addr + ub * bufcols + (uint32_t)(rb * 2 * a.tg + c0);
                 float x[8], y[8];
                 tmem_ld8(col, x);
                 tmem_ld8(col + (uint32_t)T, y);
@@ -946,8 +955,13 @@ struct TcShape {
 TcShape tc_shape(int32_t nrhs, int optin, int np) {
     TcShape s;
     s.rb_count = (nrhs + 63) / 64;
-    // one accumulator per G set (rb_count blocks x 2T columns) in each of two unit buffers
-    s.tg = (kSetCols / (2 * kSets * s.rb_count)) / 8 * 8;
+    // One accumulator per G set (rb_count blocks x 2T columns) in each unit buffer.  The hi/lo split keeps two
+    // buffers of 32-target units, so the epilogue of one unit overlaps the MMAs of the next.  The three-part
+    // split takes 64-target units in one buffer (all 512 columns): a box of 33 - 64 targets is one unit instead
+    // of two walking the same list, and its six MMAs per stage leave the epilogue's wait a smaller share (the
+    // ellipsoid at 64 RHS: 7.14 ms against 7.64; hi/lo with the same shape 5.46 against 5.11).
+    const int units_in_tmem = np == 3 ? 1 : 2;
+    s.tg = (2 * kSetCols / (units_in_tmem * 2 * kSets * s.rb_count)) / 8 * 8;
     if (s.tg > 64) s.tg = 64;
     s.slot_bytes = slot_bytes_for(s.rb_count, s.tg, np);
     s.slots = 8;
@@ -1030,6 +1044,7 @@ p2p_status p2p_apply_tc(const p2p_plan* plan, float2* out, int32_t nrhs, int64_t
     a.slots = sh.slots;
     a.slot_bytes = sh.slot_bytes;
     a.np = np;
+    a.nbuf = 512 / (kSets * 2 * sh.tg * sh.rb_count);
     a.k = adjoint ? -plan->k : plan->k;
     a.status = plan->status;
     a.wait_limit = plan->tc_wait_polls < 0 ? kWaitLimit : (uint32_t)plan->tc_wait_polls;
