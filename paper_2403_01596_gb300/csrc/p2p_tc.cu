@@ -65,8 +65,10 @@ constexpr int kImage = 2 * kPart;      // hi + lo images (the operand self-check
 constexpr int kLbo = 128, kSbo = 256;  // core-matrix strides (K direction, 8-row groups)
 constexpr int kSetCols = 256;          // TMEM columns of a unit buffer of 32-target units (an accumulator per set)
 // G sets (independent producer -> G -> MMA chains; 2 or 4, the group lists are
-// padded to multiples of 4).  Four sets of four warps measured twice as fast as
-// two sets of eight (units of up to 64 targets, half the stages).
+// padded to multiples of 4).  On the 2^21-point ellipsoid at 64 RHS four sets of
+// four warps measured 5.1 ms against 5.3 for two sets of eight with units of up
+// to 64 targets; two sets would also halve the accumulators of the three-part
+// split, whose error grows with the accumulation chains.
 #ifndef P2P_TC_SETS
 #define P2P_TC_SETS 4
 #endif
