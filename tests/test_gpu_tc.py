@@ -163,17 +163,19 @@ def test_tc_full_size_ellipsoid_sampled():
     assert rel_l2(out[targets], ref).max() <= TOL
 
 
-@pytest.mark.parametrize("path", TC_PATHS)
-def test_tc_two_target_groups_per_box(path):
-    """Boxes of 33 - 64 targets (two units of up to 32 targets each) on a grid of one CTA per SM: every round of
-    the grid covers whole boxes, and the units' target groups rotate between rounds.  The 2^20-point sphere at
-    16 points per box (max 50): sampled targets against the oracle, all targets against the FP32 path."""
+@pytest.mark.parametrize("path,occupancy", [("tc_bf16x3", 16), ("tc_bf16x6", 32)])
+def test_tc_two_target_groups_per_box(path, occupancy):
+    """Two units per box on a grid of one CTA per SM (152 SMs: every round of the grid covers whole boxes, and
+    the units' target groups rotate between rounds): the hi/lo split's 32-target units on the 2^20-point sphere
+    at 16 points per box (max 50), the three-part split's 64-target units at 32 points per box (max 90); sampled
+    targets against the oracle, all targets against the FP32 path."""
     api = _api()
-    wl = W.sphere_density(16)
+    wl = W.sphere_density(occupancy)
     nrhs = 64
     lam = W.strengths(wl.n, nrhs, 12)
     plan = api.Plan(torch.from_numpy(wl.points).cuda(), wl.lo, wl.h, wl.ng, wl.k, max_nrhs=nrhs)
-    assert 32 < int(torch.diff(plan.structure.box_ptr.long()).max().item()) <= 64
+    unit = 32 if path == "tc_bf16x3" else 64
+    assert unit < int(torch.diff(plan.structure.box_ptr.long()).max().item()) <= 2 * unit
     lam_d = torch.from_numpy(lam).cuda()
     out = plan.apply(lam_d, path=path).cpu().numpy()
     assert plan.async_status() == 0
